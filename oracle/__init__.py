@@ -1,0 +1,244 @@
+"""FP64 CPU oracle for the ray-casting volume renderer (test infrastructure).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg (and its ``--impl reference`` arm) may import this package.  It shares no code
+with the CUDA renderer; both consume the same inputs from ``synth``.
+
+What it computes (steps in order; the paper -- Hassan, Fluke & Barnes, Abstract
+and Secs. 1 and 3 -- names ray casting of spectral cubes, larger-than-memory
+decomposition and high-resolution renders of one orientation, but prints no
+formulas, so each step is the standard definition):
+
+1. camera ray per pixel centre (rows top-down; orthographic rays start on the
+   image plane, perspective rays at the eye);
+2. slab intersection with [0,nx]x[0,ny]x[0,nz], t >= 0;
+3. samples t_k = k*step, k in [ceil(t_near/step), ceil(t_far/step));
+4. trilinear interpolation, cell-centred voxels, clamp to edge;
+5. node-centred linear transfer-function lookup over [vmin, vmax], clamped;
+6. front-to-back "over" with termination after the sample at which
+   1 - T >= ert; MIP outputs TF(max v) straight;
+7. the adjoint of 6 (reverse sweep with suffix colour / transmittance).
+
+Parity pins: see tests/test_oracle_pins.py (closed forms for constant cubes,
+single-peak MIP, brute force along the spectral axis, sort-last invariance,
+finite differences for the adjoint).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_oracle.so (gcc -O2, strict IEEE: no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-std=gnu11",
+                               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrcCamera(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("eye", ctypes.c_double * 3), ("right", ctypes.c_double * 3),
+                ("up", ctypes.c_double * 3), ("fwd", ctypes.c_double * 3),
+                ("win", ctypes.c_double * 4), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class OrcScene(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("vol", ctypes.c_void_p), ("tf", ctypes.c_void_p), ("ntf", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double),
+                ("step", ctypes.c_double), ("ert", ctypes.c_double), ("dk0", ctypes.c_int32),
+                ("dk1", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            lib.orc_render.restype = ctypes.c_int
+            lib.orc_render.argtypes = [_P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_int]
+            lib.orc_render_sortlast.restype = ctypes.c_int
+            lib.orc_render_sortlast.argtypes = [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P,
+                                                _P, ctypes.c_int]
+            lib.orc_backward.restype = ctypes.c_int
+            lib.orc_backward.argtypes = [_P, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_int]
+            lib.orc_touch.restype = ctypes.c_int
+            lib.orc_touch.argtypes = [_P, _P, _P, ctypes.c_int64, _P, ctypes.c_int]
+            lib.orc_round_bf16.restype = None
+            lib.orc_round_bf16.argtypes = [_P, _P, ctypes.c_int64]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def camera_struct(cam: dict) -> OrcCamera:
+    c = OrcCamera()
+    c.type = int(cam["type"])
+    for k in ("eye", "right", "up", "fwd"):
+        setattr(c, k, (ctypes.c_double * 3)(*[float(v) for v in cam[k]]))
+    c.win = (ctypes.c_double * 4)(*[float(v) for v in cam["win"]])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+class Scene:
+    """A cube (float32 values as stored), a transfer function and march settings."""
+
+    def __init__(self, vol: np.ndarray, tf: np.ndarray, vmin: float, vmax: float,
+                 step: float = 0.5, ert: float = 0.99):
+        vol = np.ascontiguousarray(vol, dtype=np.float32)
+        tf = np.ascontiguousarray(tf, dtype=np.float32)
+        assert vol.ndim == 3 and tf.ndim == 2 and tf.shape[1] == 4 and tf.shape[0] >= 2
+        self.vol, self.tf = vol, tf
+        self.nz, self.ny, self.nx = vol.shape
+        self.vmin, self.vmax, self.step, self.ert = float(vmin), float(vmax), float(step), float(ert)
+
+    def _struct(self, mode: int, ert=None, dk0=0, dk1=0) -> OrcScene:
+        s = OrcScene()
+        s.nx, s.ny, s.nz = self.nx, self.ny, self.nz
+        s.vol, s.tf = self.vol.ctypes.data, self.tf.ctypes.data
+        s.ntf, s.mode = self.tf.shape[0], int(mode)
+        s.vmin, s.vmax, s.step = self.vmin, self.vmax, self.step
+        s.ert = self.ert if ert is None else float(ert)
+        s.dk0, s.dk1 = int(dk0), int(dk1)
+        return s
+
+
+def _nthreads(n):
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def render(scene: Scene, cam: dict, mode: str = "composite", pixels=None, *, ert=None, dk0=0,
+           dk1=0, nthreads=None) -> dict:
+    """Render pixels (flat py*W+px; None = whole image) -> dict(rgba, max, nsamples, flags)."""
+    lib = _load()
+    m = {"composite": 0, "mip": 1}[mode]
+    s = scene._struct(m, ert, dk0, dk1)
+    c = camera_struct(cam)
+    if pixels is None:
+        npix = cam["width"] * cam["height"]
+        pix = None
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64)
+        npix = pix.size
+    rgba = np.zeros((npix, 4), np.float64)
+    vmax = np.zeros(npix, np.float64)
+    ns = np.zeros(npix, np.int64)
+    fl = np.zeros(npix, np.int32)
+    rc = lib.orc_render(ctypes.byref(s), ctypes.byref(c), None if pix is None else _ptr(pix),
+                        npix, _ptr(rgba), _ptr(vmax), _ptr(ns), _ptr(fl), _nthreads(nthreads))
+    if rc:
+        raise ValueError("orc_render: bad arguments")
+    return dict(rgba=rgba, max=vmax, nsamples=ns, flags=fl)
+
+
+def render_sortlast(scene: Scene, cam: dict, brick: int, mode: str = "composite", pixels=None,
+                    *, ert=None, nthreads=None) -> dict:
+    lib = _load()
+    m = {"composite": 0, "mip": 1}[mode]
+    s = scene._struct(m, ert)
+    c = camera_struct(cam)
+    if pixels is None:
+        npix, pix = cam["width"] * cam["height"], None
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64)
+        npix = pix.size
+    rgba = np.zeros((npix, 4), np.float64)
+    vmax = np.zeros(npix, np.float64)
+    rc = lib.orc_render_sortlast(ctypes.byref(s), ctypes.byref(c), int(brick),
+                                 None if pix is None else _ptr(pix), npix, _ptr(rgba), _ptr(vmax),
+                                 _nthreads(nthreads))
+    if rc:
+        raise ValueError("orc_render_sortlast: bad arguments")
+    return dict(rgba=rgba, max=vmax)
+
+
+def backward(scene: Scene, cams: list, dimg: np.ndarray, mode: str = "composite", *,
+             with_volume=True, ert=None, nthreads=None):
+    """dL/dTF (ntf x 4) and dL/dvol (nz, ny, nx) for dL/dI = dimg (ncams, H, W, 4)."""
+    lib = _load()
+    m = {"composite": 0, "mip": 1}[mode]
+    s = scene._struct(m, ert)
+    arr = (OrcCamera * len(cams))(*[camera_struct(c) for c in cams])
+    g = np.ascontiguousarray(dimg, dtype=np.float64)
+    assert g.shape == (len(cams), cams[0]["height"], cams[0]["width"], 4)
+    dtf = np.zeros((scene.tf.shape[0], 4), np.float64)
+    dvol = np.zeros(scene.vol.shape, np.float64) if with_volume else None
+    nt = _nthreads(nthreads)
+    if with_volume:  # one voxel accumulator per thread
+        nt = max(1, min(nt, int(4e9 // max(1, dvol.nbytes))))
+    rc = lib.orc_backward(ctypes.byref(s), arr, len(cams), _ptr(g), _ptr(dtf),
+                          None if dvol is None else _ptr(dvol), nt)
+    if rc:
+        raise ValueError("orc_backward: bad arguments")
+    return dtf, dvol
+
+
+def touched(scene: Scene, cam: dict, mode: str = "mip", pixels=None, nthreads=None) -> np.ndarray:
+    """Byte mask (nz, ny, nx) of the voxels read by the executed samples."""
+    lib = _load()
+    m = {"composite": 0, "mip": 1}[mode]
+    s = scene._struct(m)
+    c = camera_struct(cam)
+    mask = np.zeros(scene.vol.shape, np.uint8)
+    if pixels is None:
+        npix, pix = cam["width"] * cam["height"], None
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int64)
+        npix = pix.size
+    rc = lib.orc_touch(ctypes.byref(s), ctypes.byref(c), None if pix is None else _ptr(pix), npix,
+                       _ptr(mask), _nthreads(nthreads))
+    if rc:
+        raise ValueError("orc_touch: bad arguments")
+    return mask
+
+
+def round_storage(vol: np.ndarray, storage: str) -> np.ndarray:
+    """The float32 cube as the renderer stores it: 'f32' unchanged, 'f16' IEEE binary16,
+    'bf16' bfloat16, both round-to-nearest-even, returned widened to float32."""
+    vol = np.ascontiguousarray(vol, dtype=np.float32)
+    if storage == "f32":
+        return vol
+    if storage == "f16":
+        return vol.astype(np.float16).astype(np.float32)
+    if storage == "bf16":
+        out = np.empty_like(vol)
+        _load().orc_round_bf16(_ptr(vol), _ptr(out), vol.size)
+        return out
+    raise ValueError(storage)
+
+
+def l2_loss(img: np.ndarray, target: np.ndarray):
+    """L = mean((I - I*)^2) over every value, and dL/dI."""
+    d = np.asarray(img, np.float64) - np.asarray(target, np.float64)
+    return float(np.mean(d * d)), 2.0 * d / d.size
+
+
+def variants(flags: int):
+    """(ert shift, dk0, dk1) combinations that a flagged ray may legitimately take."""
+    k0s = (0, -1, 1) if flags & 1 else (0,)
+    k1s = (0, -1, 1) if flags & 2 else (0,)
+    es = (0.0, -2e-5, 2e-5) if flags & 4 else (0.0,)
+    return [(e, a, b) for e in es for a in k0s for b in k1s]

@@ -1,0 +1,299 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test fixes one part of the method by a closed form, a library routine, brute
+force written differently from the oracle, or an invariant of the mathematics:
+
+* constant cube: accumulated alpha 1-(1-a)^n and colour rgb*(1-(1-a)^n), with n from
+  hand-derived ray/box chords; with termination n_ERT = ceil(ln 0.01 / ln(1-a));
+* transfer function: numpy.interp over the node grid, clamped;
+* single-peak MIP: the peak value, and the trilinear hat off-centre;
+* axis-aligned views: numpy brute force along the spectral axis, composited by the
+  closed-form product sum_j a_j c_j prod_{i<j}(1 - a_i) and cumulative products;
+* sort-last: partial images per brick folded in visibility order equal the direct
+  render (associativity of "over"; max is exact);
+* 5 x 5 style mosaic: sub-frusta equal the crops of the one big render;
+* adjoint: central finite differences of the FP64 loss;
+* bfloat16 rounding: torch's conversion and hand-made ties.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+TOL = 1e-12
+
+
+def cam(type_, eye, fwd, right=(1, 0, 0), up=(0, 1, 0), win=(-0.5, 0.5, -0.5, 0.5), w=1, h=1):
+    return dict(type=type_, eye=list(eye), right=list(right), up=list(up), fwd=list(fwd),
+                win=list(win), width=w, height=h)
+
+
+# ------------------------------------------------------------------------- constant cube
+@pytest.mark.parametrize("a", [0.02, 0.1, 0.37, 0.8])
+def test_constant_cube_closed_form(a):
+    vol = np.full((10, 6, 8), 3.0, np.float32)  # nz, ny, nx
+    a32 = float(np.float32(a))
+    rgb = np.array([0.2, 0.5, 0.9], np.float32).astype(np.float64)
+    tf = np.tile(np.array([0.2, 0.5, 0.9, a], np.float32), (5, 1))
+    s = 1 / math.sqrt(2)
+    rays = [
+        # orthographic along +z from z = -1.3: t in [1.3, 11.3) -> k = 3..22 (20 samples)
+        (cam(0, (4.1, 2.2, -1.3), (0, 0, 1)), 20),
+        # orthographic along (1,0,1)/sqrt2 from (-2, 3.3, -1): enters x=0 at t=2 sqrt2,
+        # leaves x=8 at t=10 sqrt2 -> k = ceil(5.657)=6 .. ceil(28.28)-1=28 (23 samples)
+        (cam(0, (-2, 3.3, -1), (s, 0, s), right=(s, 0, -s)), 23),
+        # perspective along +z from z = -5.2: t in [5.2, 15.2) -> k = 11..30 (20 samples)
+        (cam(1, (4, 3, -5.2), (0, 0, 1)), 20),
+    ]
+    for c, n in rays:
+        sc = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5, ert=2.0)
+        r = oracle.render(sc, c, "composite")
+        assert r["nsamples"][0] == n
+        A = 1 - (1 - a32) ** n
+        np.testing.assert_allclose(r["rgba"][0, 3], A, atol=TOL)
+        np.testing.assert_allclose(r["rgba"][0, :3], rgb * A, atol=TOL)
+        # early termination at accumulated alpha 0.99
+        sc = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5, ert=0.99)
+        r = oracle.render(sc, c, "composite")
+        n_ert = min(n, math.ceil(math.log(0.01) / math.log(1 - a32)))
+        assert r["nsamples"][0] == n_ert
+        np.testing.assert_allclose(r["rgba"][0, 3], 1 - (1 - a32) ** n_ert, atol=TOL)
+
+
+def test_empty_ray_and_miss():
+    vol = np.ones((4, 4, 4), np.float32)
+    tf = synth.viridis_ramp_tf(8)
+    sc = oracle.Scene(vol, tf, 0.0, 2.0)
+    miss = cam(1, (10, 10, -5), (0, 0, 1))
+    for mode in ("composite", "mip"):
+        r = oracle.render(sc, miss, mode)
+        assert r["nsamples"][0] == 0 and np.all(r["rgba"] == 0)
+    assert oracle.render(sc, miss, "mip")["max"][0] == -np.inf
+
+
+# --------------------------------------------------------------------- transfer function
+def test_tf_lookup_matches_numpy_interp():
+    tf = synth.hidden_tf(3, n=17)
+    vmin, vmax = -1.0, 20.0
+    nodes = np.linspace(vmin, vmax, tf.shape[0])
+    for val in [-5.0, -1.0, -0.3, 0.0, 2.7, 7.77, 19.99, 20.0, 33.0]:
+        vol = np.full((3, 3, 3), val, np.float32)
+        sc = oracle.Scene(vol, tf, vmin, vmax)
+        r = oracle.render(sc, cam(0, (1.5, 1.5, -0.7), (0, 0, 1)), "mip")
+        v32 = float(np.float32(val))
+        want = [np.interp(v32, nodes, tf[:, c].astype(np.float64)) for c in range(4)]
+        np.testing.assert_allclose(r["rgba"][0], want, atol=1e-12)
+        assert r["max"][0] == v32
+
+
+# ---------------------------------------------------------------------- single-peak MIP
+@pytest.mark.parametrize("dx,dy", [(0.0, 0.0), (0.3, 0.0), (-0.2, 0.45)])
+def test_single_peak_mip(dx, dy):
+    vol = np.zeros((9, 9, 9), np.float32)
+    V = 7.0
+    vol[4, 4, 4] = V  # centre (4.5, 4.5, 4.5)
+    tf = synth.viridis_ramp_tf()
+    sc = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5)
+    # image plane z = -1: samples at z = -1 + k/2, one of them exactly at z = 4.5
+    r = oracle.render(sc, cam(0, (4.5 + dx, 4.5 + dy, -1.0), (0, 0, 1)), "mip")
+    np.testing.assert_allclose(r["max"][0], V * (1 - abs(dx)) * (1 - abs(dy)), atol=1e-12)
+    # plane z = -0.75: nearest samples at 4.25 / 4.75 -> hat value 0.75 along z
+    r = oracle.render(sc, cam(0, (4.5 + dx, 4.5 + dy, -0.75), (0, 0, 1)), "mip")
+    np.testing.assert_allclose(r["max"][0], V * (1 - abs(dx)) * (1 - abs(dy)) * 0.75, atol=1e-12)
+
+
+# ------------------------------------------------------- axis-aligned brute force (numpy)
+def _column_view(nx, ny, xoff, z0):
+    # orthographic down +z; pixel (px, py) at x = px + 0.5 + xoff, y = ny - 0.5 - py
+    return dict(type=0, eye=[0.0, 0.0, z0], right=[1, 0, 0], up=[0, 1, 0], fwd=[0, 0, 1],
+                win=[xoff, xoff + (nx - 1), 0.0, float(ny)], width=nx - 1, height=ny)
+
+
+def _brute(vol, tf, vmin, vmax, xoff, z0, step, ert):
+    nz, ny, nx = vol.shape
+    W, H = nx - 1, ny
+    nodes = np.linspace(vmin, vmax, tf.shape[0])
+    t_near, t_far = -z0, nz - z0
+    ks = np.arange(math.ceil(t_near / step), math.ceil(t_far / step))
+    zs = z0 + ks * step
+    img = np.zeros((H, W, 4))
+    mip = np.zeros((H, W))
+    for py in range(H):
+        y = ny - 1 - py
+        for px in range(W):
+            fx = xoff
+            col = (1 - fx) * vol[:, y, px].astype(np.float64) + fx * vol[:, y, px + 1]
+            vals = np.interp(zs - 0.5, np.arange(nz), col)  # clamps at both ends
+            mip[py, px] = vals.max()
+            rgba = np.stack([np.interp(vals, nodes, tf[:, c].astype(np.float64))
+                             for c in range(4)], 1)
+            a = rgba[:, 3]
+            trans = np.cumprod(1 - a)                      # T after each sample
+            n = len(a)
+            if ert <= 1:
+                hit = np.nonzero(1 - trans >= ert)[0]
+                if len(hit):
+                    n = hit[0] + 1
+            before = np.concatenate([[1.0], trans[:-1]])   # prod_{i<j} (1 - a_i)
+            img[py, px, :3] = (a[:n, None] * rgba[:n, :3] * before[:n, None]).sum(0)
+            img[py, px, 3] = 1 - trans[n - 1]
+    return img, mip
+
+
+@pytest.mark.parametrize("step,z0,xoff", [(1.0, -2.25, 0.0), (0.5, -2.3, 0.3), (0.25, -0.6, 0.7)])
+@pytest.mark.parametrize("ert", [2.0, 0.99])
+def test_axis_aligned_bruteforce(step, z0, xoff, ert):
+    rng = np.random.default_rng(11)
+    nz, ny, nx = 14, 5, 7
+    vol = rng.normal(size=(nz, ny, nx)).astype(np.float32) * 4 + 3
+    tf = synth.viridis_ramp_tf()
+    sc = oracle.Scene(vol, tf, -1.0, 20.0, step=step, ert=ert)
+    c = _column_view(nx, ny, xoff, z0)
+    want, wmip = _brute(vol, tf, -1.0, 20.0, xoff, z0, step, ert)
+    r = oracle.render(sc, c, "composite")
+    assert not np.any(r["flags"] & 3)
+    np.testing.assert_allclose(r["rgba"].reshape(ny, nx - 1, 4), want, atol=1e-12)
+    r = oracle.render(sc, c, "mip")
+    np.testing.assert_allclose(r["max"].reshape(ny, nx - 1), wmip, atol=1e-12)
+
+
+# ------------------------------------------------------------------ sort-last invariance
+def _small_scene(ert=2.0, seed=5, dims=(20, 17, 23)):
+    p = synth.cube_params(*dims, seed=seed, nsrc=4, ripple=True, ripple_period=16.0)
+    vol = synth.generate(p)
+    return oracle.Scene(vol, synth.viridis_ramp_tf(), -1.0, 20.0, step=0.5, ert=ert)
+
+
+@pytest.mark.parametrize("brick", [4, 8, 16])
+def test_sortlast_equals_direct(brick):
+    sc = _small_scene()
+    dims = (sc.nx, sc.ny, sc.nz)
+    views = [synth.ortho_view(dims, 24, 20), synth.orbit_view(dims, 40.0, 24, 20),
+             synth.random_views(dims, 1, seed=3, width=24, height=20)[0]]
+    for v in views:
+        d = oracle.render(sc, v, "composite")
+        s = oracle.render_sortlast(sc, v, brick, "composite")
+        np.testing.assert_allclose(s["rgba"], d["rgba"], atol=1e-12)
+        d = oracle.render(sc, v, "mip")
+        s = oracle.render_sortlast(sc, v, brick, "mip")
+        assert np.array_equal(s["max"], d["max"])
+        assert np.array_equal(s["rgba"], d["rgba"])
+
+
+def test_termination_changes_at_most_one_percent():
+    sc = _small_scene(ert=0.99)
+    dims = (sc.nx, sc.ny, sc.nz)
+    v = synth.orbit_view(dims, 20.0, 32, 24)
+    on = oracle.render(sc, v, "composite")["rgba"]
+    off = oracle.render(sc, v, "composite", ert=2.0)["rgba"]
+    assert np.max(np.abs(on - off)) <= 0.01 + 1e-12
+
+
+# ------------------------------------------------------------------------------ mosaic
+def test_mosaic_equals_big_render():
+    sc = _small_scene(ert=0.99)
+    dims = (sc.nx, sc.ny, sc.nz)
+    big = synth.orbit_view(dims, 25.0, 5 * 8, 5 * 6)
+    full = oracle.render(sc, big, "composite")["rgba"].reshape(30, 40, 4)
+    for i, p in enumerate(synth.wall_views(big, 5, 5)):
+        rr, cc = divmod(i, 5)
+        part = oracle.render(sc, p, "composite")["rgba"].reshape(6, 8, 4)
+        np.testing.assert_allclose(part, full[6 * rr:6 * rr + 6, 8 * cc:8 * cc + 8], atol=1e-9)
+
+
+# ------------------------------------------------------------------------------ adjoint
+def _loss(sc, views, target, mode):
+    imgs = np.stack([oracle.render(sc, v, mode)["rgba"].reshape(v["height"], v["width"], 4)
+                     for v in views])
+    return oracle.l2_loss(imgs, target)
+
+
+def _nsamp(sc, views, mode):
+    return np.concatenate([oracle.render(sc, v, mode)["nsamples"] for v in views])
+
+
+@pytest.mark.parametrize("mode", ["composite", "mip"])
+def test_adjoint_matches_finite_differences(mode):
+    p = synth.cube_params(12, 10, 9, seed=21, nsrc=3)
+    vol = synth.generate(p)
+    tf = synth.viridis_ramp_tf(32)
+    sc = oracle.Scene(vol, tf, -1.0, 20.0, step=0.5, ert=0.99)
+    views = synth.random_views((12, 10, 9), 2, seed=4, width=12, height=10)
+    tsc = oracle.Scene(vol, synth.hidden_tf(99, 32), -1.0, 20.0, step=0.5, ert=0.99)
+    target = np.stack([oracle.render(tsc, v, mode)["rgba"].reshape(10, 12, 4) for v in views])
+    L0, dimg = _loss(sc, views, target, mode)
+    dtf, dvol = oracle.backward(sc, views, dimg.reshape(2, 10, 12, 4), mode)
+    base_ns = _nsamp(sc, views, mode)
+    rng = np.random.default_rng(1)
+
+    def fd(perturb):
+        lp, ln_ = [], []
+        for sgn, acc in ((1, lp), (-1, ln_)):
+            s2, h = perturb(sgn)
+            if not np.array_equal(_nsamp(s2, views, mode), base_ns):
+                return None
+            acc.append((_loss(s2, views, target, mode)[0], h))
+        (l1, h1), (l2, h2) = lp[0], ln_[0]
+        return (l1 - l2) / (h1 - h2)
+
+    checked = 0
+    cand = [tuple(x) for x in np.argwhere(np.abs(dtf) > 1e-6 * np.abs(dtf).max())]
+    rng.shuffle(cand)
+    gmax = np.abs(dtf).max()
+    for (i, c) in cand[:12]:
+        def pert(sgn, i=i, c=c):
+            t2 = tf.copy()
+            t2[i, c] = np.float32(tf[i, c] + sgn * 1e-3)
+            return oracle.Scene(vol, t2, -1.0, 20.0, 0.5, 0.99), float(t2[i, c]) - float(tf[i, c])
+        g = fd(pert)
+        if g is None:
+            continue
+        rel = abs(g - dtf[i, c]) / max(abs(g), 1e-2 * gmax)
+        assert rel <= 1e-3, (i, c, g, dtf[i, c])
+        checked += 1
+    assert checked >= 6
+    vmaxg = np.abs(dvol).max()
+    cand = [tuple(x) for x in np.argwhere(np.abs(dvol) > 1e-3 * vmaxg)]
+    rng.shuffle(cand)
+    checked = 0
+    for idx in cand[:12]:
+        def pertv(sgn, idx=idx):
+            v2 = vol.copy()
+            v2[idx] = np.float32(vol[idx] + sgn * 1e-3)
+            return oracle.Scene(v2, tf, -1.0, 20.0, 0.5, 0.99), float(v2[idx]) - float(vol[idx])
+        g = fd(pertv)
+        if g is None:
+            continue
+        rel = abs(g - dvol[idx]) / max(abs(g), 1e-2 * vmaxg)
+        assert rel <= 1e-3, (idx, g, dvol[idx])
+        checked += 1
+    assert checked >= 6
+
+
+# ---------------------------------------------------------------------- touched voxels
+def test_touch_census_axis_ray():
+    vol = np.zeros((6, 5, 4), np.float32)
+    sc = oracle.Scene(vol, synth.viridis_ramp_tf(), 0.0, 1.0)
+    # one ray down +z through voxel centre (1.5, 2.5): corners x in {1,2}, y in {2,3}
+    m = oracle.touched(sc, cam(0, (1.5, 2.5, -0.7), (0, 0, 1)), "mip")
+    want = np.zeros_like(m)
+    want[:, 2:4, 1:3] = 1
+    assert np.array_equal(m, want)
+
+
+# ---------------------------------------------------------------------- storage rounding
+def test_bf16_rounding():
+    torch = pytest.importorskip("torch")
+    x = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, -2.5, 1e-30, 3.0e38, 0.1, 19.37],
+                 np.float32)
+    got = oracle.round_storage(x, "bf16")
+    assert got[0] == 1.0 and got[1] == 1 + 2 ** -6  # ties to even
+    rng = np.random.default_rng(0)
+    y = (rng.normal(size=10000) * 10).astype(np.float32)
+    want = torch.from_numpy(y).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(oracle.round_storage(y, "bf16"), want)
+    assert np.array_equal(oracle.round_storage(y, "f16"),
+                          torch.from_numpy(y).to(torch.float16).to(torch.float32).numpy())
