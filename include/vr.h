@@ -1,0 +1,177 @@
+/*
+ * vr.h -- C ABI of the GB300 (sm_103a) ray-casting volume renderer for
+ * spectral data cubes.
+ *
+ * The method is the ray-casting renderer of Hassan, Fluke & Barnes,
+ * "Distributed GPU Volume Rendering of ASKAP Spectral Data Cubes":
+ *   - Abstract and Sec. 1: real-time ray casting of HI spectral cubes larger
+ *     than one machine's memory, by decomposing the cube;
+ *   - Sec. 3: a static render of the current orientation at a user-defined
+ *     output size, e.g. the 5 x 5 wall of 1920 x 1080 panels (9600 x 5400).
+ * The paper prints no formulas.  The operations below are the standard
+ * front-to-back emission-absorption ray caster; each entry point states the
+ * exact discretisation it computes.
+ *
+ * Conventions for every entry point:
+ *   - The caller owns every pointer it passes.  The library copies the cube,
+ *     the transfer function and the cameras, and keeps no caller pointer after
+ *     an entry point returns.
+ *   - "stream" is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     outputs are written in stream order and are valid once the caller has
+ *     synchronised that stream.
+ *   - No C++ exception crosses this boundary.  Every failure is a status code;
+ *     vr_last_error() returns a human-readable message for the last failing
+ *     call on a context.  An asynchronous CUDA error surfaces as VR_ERR_CUDA
+ *     on a later call.
+ *   - A context is bound to one device.  Entry points make that device current
+ *     for their duration and restore the caller's current device on return.
+ *   - Calls on one context are not thread-safe; use one context per thread.
+ */
+#ifndef VR_H
+#define VR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VR_ABI_VERSION 1
+
+typedef enum {
+    VR_OK = 0,
+    VR_ERR_INVALID_ARG = 1, /* a pointer, size or enum is out of range      */
+    VR_ERR_STATE = 2,       /* e.g. render before a cube/camera/TF is set  */
+    VR_ERR_OOM = 3,         /* device or pinned-host allocation failed     */
+    VR_ERR_CUDA = 4,        /* a CUDA runtime call failed                  */
+    VR_ERR_TIMEOUT = 5,     /* a bounded host wait expired                 */
+    VR_ERR_IO = 6,          /* a caller-supplied data source failed        */
+    VR_ERR_INTERNAL = 7,    /* a device-side check recorded an error       */
+    VR_ERR_UNSUPPORTED = 8  /* valid request this build does not implement */
+} vr_status;
+
+/* Storage type of the bricked cube.  Sampling and compositing are FP32. */
+typedef enum { VR_F32 = 0, VR_F16 = 1, VR_BF16 = 2 } vr_dtype;
+
+/* VR_COMPOSITE: front-to-back "over" with early termination, premultiplied
+ * RGBA output.  VR_MIP: maximum-intensity projection, output TF(max) as
+ * straight RGBA. */
+typedef enum { VR_COMPOSITE = 0, VR_MIP = 1 } vr_mode;
+
+/*
+ * Camera.  Pixel (px, py), py = 0 the top row, has window coordinates
+ *     u = win[0] + (px + 1/2) (win[1] - win[0]) / width
+ *     v = win[3] - (py + 1/2) (win[3] - win[2]) / height
+ * type 0 (orthographic): origin eye + u right + v up, direction fwd.
+ * type 1 (perspective):  origin eye, direction fwd + u right + v up
+ *     (win is a tangent-space window: an off-axis sub-window of a larger
+ *     view, such as one panel of a tiled wall, is just a smaller win).
+ * Directions are normalised; samples lie at t = k * step along the unit
+ * direction from the origin, k integer (Sec. 3's "same orientation, other
+ * output size" is the same camera with another width/height).
+ * All cameras passed together must have the same width and height.
+ */
+typedef struct {
+    int32_t type;
+    int32_t pad_;
+    double eye[3], right[3], up[3], fwd[3];
+    double win[4]; /* l, r, b, t */
+    int32_t width, height;
+} vr_camera;
+
+typedef struct {
+    int32_t brick;  /* interior brick edge in voxels, power of two in [8, 256];
+                       default 128.  Bricks carry a 1-voxel ghost layer.    */
+    int32_t pad_;
+    double step;    /* sample spacing along the ray in voxels, > 0; default 0.5 */
+    double ert;     /* early termination once accumulated alpha >= ert after a
+                       sample; default 0.99; a value > 1 disables it          */
+} vr_options;
+
+typedef struct vr_ctx vr_ctx;
+
+/* Layout facts of the loaded cube (for byte accounting by callers). */
+typedef struct {
+    int64_t nx, ny, nz;      /* voxels                                    */
+    int32_t nbx, nby, nbz;   /* bricks per axis                           */
+    int32_t brick;           /* interior edge                             */
+    int32_t pitch;           /* x pitch of a stored brick row, elements   */
+    int32_t dtype;           /* vr_dtype                                  */
+    int64_t brick_bytes;     /* bytes of one stored brick slot            */
+    int64_t store_bytes;     /* bytes of the whole brick store            */
+} vr_cube_info;
+
+/* Fill *opt with the defaults (brick 128, step 0.5, ert 0.99). */
+void vr_default_options(vr_options* opt);
+
+/* Human-readable name of a status code (static storage). */
+const char* vr_status_string(vr_status s);
+
+/* Create a context on CUDA device `device`.  opt may be NULL (defaults).
+ * Allocates the scheduler's small device scratch.  *out is set to NULL on
+ * failure. */
+vr_status vr_create(vr_ctx** out, int device, const vr_options* opt);
+
+/* Free a context and everything it owns.  NULL is accepted.  The caller must
+ * have synchronised every stream on which it used the context. */
+vr_status vr_destroy(vr_ctx* ctx);
+
+/*
+ * Load a cube of nx*ny*nz float32 values, x fastest (RA x Dec x channel),
+ * from host memory (src_on_device = 0) or device memory of the context's
+ * device (src_on_device = 1), into a device brick store of `storage` type:
+ * bricks of brick^3 interior voxels plus a 1-voxel ghost layer (edge values
+ * replicated at the cube faces), row pitch padded to 16 bytes, converted
+ * with round-to-nearest-even.  Replaces any earlier cube.  Host sources are
+ * copied in slabs of brick + 2 planes; the call returns after the copy has
+ * been issued on `stream` and a host source may be freed once it returns.
+ * Errors: VR_ERR_INVALID_ARG (NULL src, any n <= 0, bad storage),
+ * VR_ERR_OOM, VR_ERR_CUDA.
+ */
+vr_status vr_load_cube(vr_ctx* ctx, const float* src, int src_on_device, int64_t nx,
+                       int64_t ny, int64_t nz, vr_dtype storage, void* stream);
+
+/*
+ * Set the transfer function: n (2 <= n <= 1024) straight RGBA float32 entries
+ * in HOST memory, node-centred over [vmin, vmax] (entry 0 at vmin, entry n-1
+ * at vmax), linearly interpolated, clamped outside the range.  vmax > vmin.
+ */
+vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, float vmin,
+                                   float vmax);
+
+/* Set ncams (1..4096) cameras from HOST memory, all of one width x height. */
+vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams);
+
+/*
+ * Render every camera into out_rgba (DEVICE, ncams x height x width x 4
+ * float32, camera-major, rows top-down).  Per pixel:
+ *   samples p_k = o + k step d for k in [ceil(t_near/step), ceil(t_far/step)),
+ *   (t_near, t_far) the slab interval of the box [0,nx]x[0,ny]x[0,nz] with
+ *   t >= 0; trilinear interpolation of voxels centred at integer + 1/2,
+ *   clamped to the edge; transfer function as set.
+ *   VR_COMPOSITE: C += T a rgb, T *= (1 - a), stop after the sample at which
+ *     1 - T >= ert; output (C, 1 - T).
+ *   VR_MIP: m = max_k v(p_k); output TF(m) (straight), or 0 with no samples.
+ * out_max (DEVICE, ncams x height x width float32, may be NULL) receives m
+ * in VR_MIP mode (-inf with no samples); it is ignored in VR_COMPOSITE mode.
+ * Errors: VR_ERR_STATE if no cube, TF or camera is set; VR_ERR_INVALID_ARG
+ * for a NULL out_rgba or bad mode.
+ */
+vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, void* stream);
+
+/* Optional DEVICE counter (uint64) to which vr_render adds the number of
+ * samples it executed; NULL switches counting off. */
+vr_status vr_set_sample_counter(vr_ctx* ctx, unsigned long long* device_counter);
+
+/* Layout of the loaded cube; VR_ERR_STATE if none is loaded. */
+vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info);
+
+/* Message of the last failing call on ctx ("" if none); static if ctx is NULL. */
+const char* vr_last_error(const vr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VR_H */

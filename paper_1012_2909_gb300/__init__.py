@@ -1,0 +1,242 @@
+"""GB300 (sm_103a) ray-casting volume renderer for spectral data cubes.
+
+Python binding of the C ABI in ``include/vr.h`` (``libvr.so``).  Functions named
+``vr_*`` mirror the C entry points one to one and only marshal arguments; every
+step of rendering runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if ``libvr.so`` is missing or
+fails to load, every call raises.
+
+The method is the ray-casting renderer of Hassan, Fluke & Barnes (Abstract,
+Sec. 1: ray casting of HI spectral cubes larger than one machine's memory;
+Sec. 3: renders of one orientation at a user-defined size, 5 x 5 wall of
+1920 x 1080 panels).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvr.so")
+
+VR_OK, VR_ERR_INVALID_ARG, VR_ERR_STATE, VR_ERR_OOM, VR_ERR_CUDA = 0, 1, 2, 3, 4
+VR_ERR_TIMEOUT, VR_ERR_IO, VR_ERR_INTERNAL, VR_ERR_UNSUPPORTED = 5, 6, 7, 8
+VR_F32, VR_F16, VR_BF16 = 0, 1, 2
+VR_COMPOSITE, VR_MIP = 0, 1
+DTYPES = {"f32": VR_F32, "f16": VR_F16, "bf16": VR_BF16}
+MODES = {"composite": VR_COMPOSITE, "mip": VR_MIP}
+
+
+class VrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} [status {status}]")
+        self.status = status
+
+
+class vr_camera(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("eye", ctypes.c_double * 3), ("right", ctypes.c_double * 3),
+                ("up", ctypes.c_double * 3), ("fwd", ctypes.c_double * 3),
+                ("win", ctypes.c_double * 4), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class vr_options(ctypes.Structure):
+    _fields_ = [("brick", ctypes.c_int32), ("pad_", ctypes.c_int32), ("step", ctypes.c_double),
+                ("ert", ctypes.c_double)]
+
+
+class vr_cube_info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("nbx", ctypes.c_int32), ("nby", ctypes.c_int32), ("nbz", ctypes.c_int32),
+                ("brick", ctypes.c_int32), ("pitch", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("brick_bytes", ctypes.c_int64), ("store_bytes", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+# name -> (restype, argtypes); every symbol include/vr.h declares.
+SIGNATURES = {
+    "vr_default_options": (None, [_P]),
+    "vr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "vr_create": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "vr_destroy": (ctypes.c_int, [_P]),
+    "vr_load_cube": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_int, _P]),
+    "vr_set_transfer_function": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_float,
+                                                ctypes.c_float]),
+    "vr_set_camera": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "vr_render": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "vr_set_sample_counter": (ctypes.c_int, [_P, _P]),
+    "vr_get_cube_info": (ctypes.c_int, [_P, _P]),
+    "vr_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libvr.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"{path} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(ctx, status: int, what: str):
+    if status != VR_OK:
+        lib = load_library()
+        msg = lib.vr_last_error(ctx).decode() if ctx else ""
+        name = lib.vr_status_string(status).decode()
+        raise VrError(status, f"{what}: {name}: {msg}")
+
+
+def _stream_handle(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def camera_struct(cam: dict) -> vr_camera:
+    c = vr_camera()
+    c.type = int(cam["type"])
+    for k in ("eye", "right", "up", "fwd"):
+        setattr(c, k, (ctypes.c_double * 3)(*[float(v) for v in cam[k]]))
+    c.win = (ctypes.c_double * 4)(*[float(v) for v in cam["win"]])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+# ------------------------------------------------------------------ same-named entry points
+def vr_create(device: int = 0, brick: int = 128, step: float = 0.5, ert: float = 0.99):
+    lib = load_library()
+    o = vr_options()
+    lib.vr_default_options(ctypes.byref(o))
+    o.brick, o.step, o.ert = int(brick), float(step), float(ert)
+    h = ctypes.c_void_p()
+    st = lib.vr_create(ctypes.byref(h), int(device), ctypes.byref(o))
+    if st != VR_OK:
+        raise VrError(st, f"vr_create: {lib.vr_status_string(st).decode()}")
+    return h
+
+
+def vr_destroy(ctx):
+    load_library().vr_destroy(ctx)
+
+
+def vr_load_cube(ctx, src, storage: str = "f32", stream=None, device: int = 0):
+    """src: float32 numpy array (host) or torch tensor (host or device), shape (nz, ny, nx)."""
+    import torch
+    lib = load_library()
+    if isinstance(src, np.ndarray):
+        src = np.ascontiguousarray(src, dtype=np.float32)
+        ptr, on_dev, shape = src.ctypes.data, 0, src.shape
+    else:
+        if src.dtype != torch.float32 or not src.is_contiguous():
+            raise ValueError("vr_load_cube: need a contiguous float32 tensor")
+        ptr, on_dev, shape = src.data_ptr(), int(src.is_cuda), tuple(src.shape)
+    nz, ny, nx = shape
+    st = lib.vr_load_cube(ctx, ctypes.c_void_p(ptr), on_dev, nx, ny, nz, DTYPES[storage],
+                          _stream_handle(stream, device))
+    _check(ctx, st, "vr_load_cube")
+
+
+def vr_set_transfer_function(ctx, rgba, vmin: float, vmax: float):
+    lib = load_library()
+    t = np.ascontiguousarray(np.asarray(rgba, dtype=np.float32))
+    st = lib.vr_set_transfer_function(ctx, t.ctypes.data_as(_P), int(t.shape[0]), float(vmin),
+                                      float(vmax))
+    _check(ctx, st, "vr_set_transfer_function")
+
+
+def vr_set_camera(ctx, cams):
+    lib = load_library()
+    if isinstance(cams, dict):
+        cams = [cams]
+    arr = (vr_camera * len(cams))(*[camera_struct(c) for c in cams])
+    st = lib.vr_set_camera(ctx, arr, len(cams))
+    _check(ctx, st, "vr_set_camera")
+
+
+def vr_render(ctx, mode: str, out_rgba, out_max=None, stream=None, device: int = 0):
+    lib = load_library()
+    st = lib.vr_render(ctx, MODES[mode], ctypes.c_void_p(out_rgba.data_ptr()),
+                       None if out_max is None else ctypes.c_void_p(out_max.data_ptr()),
+                       _stream_handle(stream, device))
+    _check(ctx, st, "vr_render")
+
+
+def vr_set_sample_counter(ctx, counter=None):
+    lib = load_library()
+    st = lib.vr_set_sample_counter(ctx, None if counter is None else
+                                   ctypes.c_void_p(counter.data_ptr()))
+    _check(ctx, st, "vr_set_sample_counter")
+
+
+def vr_get_cube_info(ctx) -> dict:
+    lib = load_library()
+    info = vr_cube_info()
+    _check(ctx, lib.vr_get_cube_info(ctx, ctypes.byref(info)), "vr_get_cube_info")
+    return {k: getattr(info, k) for k, _ in vr_cube_info._fields_}
+
+
+# ------------------------------------------------------------------ convenience object
+class Renderer:
+    """A context plus its output buffers.  All rendering happens in libvr.so."""
+
+    def __init__(self, device: int = 0, brick: int = 128, step: float = 0.5, ert: float = 0.99):
+        import torch
+        self.device = int(device)
+        self.torch_device = torch.device("cuda", self.device)
+        self.ctx = vr_create(self.device, brick, step, ert)
+        self.cams = []
+
+    def close(self):
+        if self.ctx is not None:
+            vr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_cube(self, vol, storage="f32", stream=None):
+        vr_load_cube(self.ctx, vol, storage, stream, self.device)
+
+    def set_transfer_function(self, rgba, vmin, vmax):
+        vr_set_transfer_function(self.ctx, rgba, vmin, vmax)
+
+    def set_camera(self, cams):
+        if isinstance(cams, dict):
+            cams = [cams]
+        vr_set_camera(self.ctx, cams)
+        self.cams = list(cams)
+
+    def cube_info(self):
+        return vr_get_cube_info(self.ctx)
+
+    def render(self, mode="composite", out=None, out_max=None, with_max=False, stream=None):
+        import torch
+        n, h, w = len(self.cams), self.cams[0]["height"], self.cams[0]["width"]
+        if out is None:
+            out = torch.empty((n, h, w, 4), dtype=torch.float32, device=self.torch_device)
+        if with_max and out_max is None:
+            out_max = torch.empty((n, h, w), dtype=torch.float32, device=self.torch_device)
+        vr_render(self.ctx, mode, out, out_max, stream, self.device)
+        return (out, out_max) if with_max else out

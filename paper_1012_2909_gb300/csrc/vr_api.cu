@@ -1,0 +1,384 @@
+// C ABI of the renderer (include/vr.h): context, validation, cube loading,
+// transfer function, cameras and render dispatch.  No exception crosses the
+// boundary; every failure becomes a vr_status with a message on the context.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vr_internal.cuh"
+
+using namespace vr;
+
+struct vr_ctx {
+    int device = 0;
+    vr_options opt{};
+    std::string err;
+    int num_sms = 0;
+    // cube
+    bool has_cube = false;
+    vr_dtype dtype = VR_F32;
+    long long nx = 0, ny = 0, nz = 0;
+    int nbx = 0, nby = 0, nbz = 0, B = 0, log2B = 0, rows = 0, pitch = 0;
+    long long slot_elems = 0;
+    size_t elem = 4;
+    void* pool = nullptr;
+    int* table = nullptr;
+    unsigned int* minmax = nullptr;
+    // transfer function
+    bool has_tf = false;
+    std::vector<float4> tf;
+    float vmin = 0.f, vmax = 1.f;
+    // cameras
+    std::vector<CamDev> cams;
+    // scratch
+    int* work = nullptr;
+    int work_slots = 0;
+    unsigned long long* sample_counter = nullptr;  // caller-owned
+};
+
+namespace {
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DevGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+vr_status fail(vr_ctx* c, vr_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+vr_status cuda_fail(vr_ctx* c, cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear a sticky non-fatal error state
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA, m);
+}
+
+#define VR_CK(call, what)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+void free_cube(vr_ctx* c) {
+    if (c->pool) cudaFree(c->pool);
+    if (c->table) cudaFree(c->table);
+    if (c->minmax) cudaFree(c->minmax);
+    c->pool = nullptr;
+    c->table = nullptr;
+    c->minmax = nullptr;
+    c->has_cube = false;
+}
+
+VolDev vol_dev(const vr_ctx* c) {
+    VolDev v{};
+    v.pool = c->pool;
+    v.table = c->table;
+    v.nx = (int)c->nx;
+    v.ny = (int)c->ny;
+    v.nz = (int)c->nz;
+    v.nbx = c->nbx;
+    v.nby = c->nby;
+    v.nbz = c->nbz;
+    v.B = c->B;
+    v.log2B = c->log2B;
+    v.pitch = c->pitch;
+    v.rows = c->rows;
+    v.slot_elems = c->slot_elems;
+    return v;
+}
+
+bool finite3(const double* v) {
+    return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+}  // namespace
+
+extern "C" {
+
+void vr_default_options(vr_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->brick = 128;
+    opt->step = 0.5;
+    opt->ert = 0.99;
+}
+
+const char* vr_status_string(vr_status s) {
+    switch (s) {
+        case VR_OK: return "VR_OK";
+        case VR_ERR_INVALID_ARG: return "VR_ERR_INVALID_ARG";
+        case VR_ERR_STATE: return "VR_ERR_STATE";
+        case VR_ERR_OOM: return "VR_ERR_OOM";
+        case VR_ERR_CUDA: return "VR_ERR_CUDA";
+        case VR_ERR_TIMEOUT: return "VR_ERR_TIMEOUT";
+        case VR_ERR_IO: return "VR_ERR_IO";
+        case VR_ERR_INTERNAL: return "VR_ERR_INTERNAL";
+        case VR_ERR_UNSUPPORTED: return "VR_ERR_UNSUPPORTED";
+    }
+    return "VR_ERR_UNKNOWN";
+}
+
+vr_status vr_create(vr_ctx** out, int device, const vr_options* opt) {
+    if (!out) return VR_ERR_INVALID_ARG;
+    *out = nullptr;
+    vr_options o;
+    vr_default_options(&o);
+    if (opt) o = *opt;
+    if (o.brick < 8 || o.brick > 256 || (o.brick & (o.brick - 1)) || !(o.step > 0.0) ||
+        !std::isfinite(o.step) || !(o.ert > 0.0) || !std::isfinite(o.ert))
+        return VR_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return VR_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return VR_ERR_INVALID_ARG;
+    vr_ctx* ctx = new (std::nothrow) vr_ctx();
+    if (!ctx) return VR_ERR_OOM;
+    ctx->device = device;
+    ctx->opt = o;
+    DevGuard g(device);
+    cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        ctx->work_slots = 4096 / kMaxLaunchCams + 1;
+        e = cudaMalloc(&ctx->work, sizeof(int) * ctx->work_slots);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+    }
+    *out = ctx;
+    return VR_OK;
+}
+
+vr_status vr_destroy(vr_ctx* ctx) {
+    if (!ctx) return VR_OK;
+    {
+        DevGuard g(ctx->device);
+        free_cube(ctx);
+        if (ctx->work) cudaFree(ctx->work);
+    }
+    delete ctx;
+    return VR_OK;
+}
+
+vr_status vr_load_cube(vr_ctx* ctx, const float* src, int src_on_device, int64_t nx,
+                       int64_t ny, int64_t nz, vr_dtype storage, void* stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!src) return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube: src is NULL");
+    if (nx <= 0 || ny <= 0 || nz <= 0 || nx >= (1LL << 30) || ny >= (1LL << 30) || nz >= (1LL << 30))
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube: dimensions must be in [1, 2^30)");
+    if (storage != VR_F32 && storage != VR_F16 && storage != VR_BF16)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube: unknown storage type");
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VR_CK(cudaGetLastError(), "vr_load_cube: pending CUDA error");
+    free_cube(ctx);
+    const int B = ctx->opt.brick;
+    ctx->B = B;
+    ctx->log2B = ilog2(B);
+    ctx->nx = nx;
+    ctx->ny = ny;
+    ctx->nz = nz;
+    ctx->nbx = (int)((nx + B - 1) / B);
+    ctx->nby = (int)((ny + B - 1) / B);
+    ctx->nbz = (int)((nz + B - 1) / B);
+    ctx->dtype = storage;
+    ctx->elem = storage == VR_F32 ? 4 : 2;
+    ctx->rows = B + 2;
+    const int vec = (int)(16 / ctx->elem);
+    ctx->pitch = (ctx->rows + vec - 1) / vec * vec;
+    long long se = (long long)ctx->rows * ctx->rows * ctx->pitch;
+    const long long align = 256 / (long long)ctx->elem;
+    ctx->slot_elems = (se + align - 1) / align * align;
+    const long long nbricks = (long long)ctx->nbx * ctx->nby * ctx->nbz;
+    if (nbricks > (1LL << 30)) return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube: too many bricks");
+    const size_t pool_bytes = (size_t)nbricks * (size_t)ctx->slot_elems * ctx->elem;
+    VR_CK(cudaMalloc(&ctx->pool, pool_bytes), "vr_load_cube: brick store allocation");
+    VR_CK(cudaMalloc(&ctx->table, sizeof(int) * nbricks), "vr_load_cube: brick table allocation");
+    VR_CK(cudaMalloc(&ctx->minmax, sizeof(unsigned int) * 2 * nbricks), "vr_load_cube: range allocation");
+    {
+        std::vector<int> ident((size_t)nbricks);
+        for (long long i = 0; i < nbricks; ++i) ident[(size_t)i] = (int)i;
+        VR_CK(cudaMemcpyAsync(ctx->table, ident.data(), sizeof(int) * nbricks, cudaMemcpyHostToDevice, s),
+              "vr_load_cube: brick table upload");
+        VR_CK(cudaStreamSynchronize(s), "vr_load_cube: brick table upload");
+    }
+    VR_CK(cudaMemsetAsync(ctx->minmax, 0xff, sizeof(unsigned int) * nbricks, s), "vr_load_cube: memset");
+    VR_CK(cudaMemsetAsync(ctx->minmax + nbricks, 0, sizeof(unsigned int) * nbricks, s), "vr_load_cube: memset");
+    VolDev v = vol_dev(ctx);
+    if (src_on_device) {
+        for (int bz = 0; bz < ctx->nbz; ++bz)
+            VR_CK(launch_repack(src, 0, nz, bz, v, storage, ctx->pool, ctx->minmax, s), "vr_load_cube: repack");
+    } else {
+        const size_t plane = (size_t)nx * (size_t)ny;
+        const long long maxp = std::min<long long>(ctx->rows, nz);
+        float* stage = nullptr;
+        VR_CK(cudaMallocAsync(reinterpret_cast<void**>(&stage), plane * maxp * sizeof(float), s),
+              "vr_load_cube: staging allocation");
+        for (int bz = 0; bz < ctx->nbz; ++bz) {
+            const long long z0 = std::max<long long>((long long)bz * B - 1, 0);
+            const long long z1 = std::min<long long>((long long)bz * B + B + 1, nz);
+            cudaError_t e = cudaMemcpyAsync(stage, src + (size_t)z0 * plane, plane * (z1 - z0) * sizeof(float),
+                                            cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = launch_repack(stage, z0, z1 - z0, bz, v, storage, ctx->pool, ctx->minmax, s);
+            if (e != cudaSuccess) {
+                cudaFreeAsync(stage, s);
+                cudaStreamSynchronize(s);
+                free_cube(ctx);
+                return cuda_fail(ctx, e, "vr_load_cube: slab upload/repack");
+            }
+        }
+        VR_CK(cudaFreeAsync(stage, s), "vr_load_cube: staging free");
+    }
+    VR_CK(cudaStreamSynchronize(s), "vr_load_cube: repack");
+    ctx->has_cube = true;
+    return VR_OK;
+}
+
+vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, float vmin, float vmax) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!rgba || n < 2 || n > kMaxTF)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_transfer_function: need 2 <= n <= 1024 entries");
+    if (!std::isfinite(vmin) || !std::isfinite(vmax) || !(vmax > vmin))
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_transfer_function: need finite vmin < vmax");
+    std::vector<float4> t((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        t[(size_t)i] = make_float4(rgba[4 * i], rgba[4 * i + 1], rgba[4 * i + 2], rgba[4 * i + 3]);
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(rgba[4 * i + c]))
+                return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_transfer_function: non-finite entry");
+    }
+    ctx->tf.swap(t);
+    ctx->vmin = vmin;
+    ctx->vmax = vmax;
+    ctx->has_tf = true;
+    return VR_OK;
+}
+
+vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!cams || ncams < 1 || ncams > 4096)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: need 1 <= ncams <= 4096");
+    std::vector<CamDev> out((size_t)ncams);
+    for (int i = 0; i < ncams; ++i) {
+        const vr_camera& c = cams[i];
+        if ((c.type != 0 && c.type != 1) || c.width <= 0 || c.height <= 0 ||
+            c.width > 65536 || c.height > 65536 || c.width != cams[0].width ||
+            c.height != cams[0].height)
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: bad type or size (all cameras must share one size)");
+        if (!finite3(c.eye) || !finite3(c.right) || !finite3(c.up) || !finite3(c.fwd) ||
+            !std::isfinite(c.win[0]) || !std::isfinite(c.win[1]) || !std::isfinite(c.win[2]) ||
+            !std::isfinite(c.win[3]))
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: non-finite camera");
+        if (c.type == 0 && c.fwd[0] == 0.0 && c.fwd[1] == 0.0 && c.fwd[2] == 0.0)
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: zero forward vector");
+        CamDev& d = out[(size_t)i];
+        for (int a = 0; a < 3; ++a) {
+            d.eye[a] = c.eye[a];
+            d.right[a] = c.right[a];
+            d.up[a] = c.up[a];
+            d.fwd[a] = c.fwd[a];
+        }
+        d.l = c.win[0];
+        d.t = c.win[3];
+        d.du = (c.win[1] - c.win[0]) / (double)c.width;
+        d.dv = (c.win[3] - c.win[2]) / (double)c.height;
+        d.type = c.type;
+        d.width = c.width;
+        d.height = c.height;
+        d.pad = 0;
+    }
+    if ((long long)ncams * cams[0].width * cams[0].height > (1LL << 40))
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: too many pixels");
+    ctx->cams.swap(out);
+    return VR_OK;
+}
+
+vr_status vr_set_sample_counter(vr_ctx* ctx, unsigned long long* device_counter) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    ctx->sample_counter = device_counter;
+    return VR_OK;
+}
+
+vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info) {
+    if (!ctx || !info) return VR_ERR_INVALID_ARG;
+    if (!ctx->has_cube) return VR_ERR_STATE;
+    info->nx = ctx->nx;
+    info->ny = ctx->ny;
+    info->nz = ctx->nz;
+    info->nbx = ctx->nbx;
+    info->nby = ctx->nby;
+    info->nbz = ctx->nbz;
+    info->brick = ctx->B;
+    info->pitch = ctx->pitch;
+    info->dtype = ctx->dtype;
+    info->brick_bytes = ctx->slot_elems * (long long)ctx->elem;
+    info->store_bytes = info->brick_bytes * (long long)ctx->nbx * ctx->nby * ctx->nbz;
+    return VR_OK;
+}
+
+vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, void* stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (mode != VR_COMPOSITE && mode != VR_MIP) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: bad mode");
+    if (!out_rgba) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: out_rgba is NULL");
+    if (reinterpret_cast<uintptr_t>(out_rgba) % 16 || reinterpret_cast<uintptr_t>(out_max) % 4)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: out_rgba must be 16-byte aligned, out_max 4-byte");
+    if (!ctx->has_cube) return fail(ctx, VR_ERR_STATE, "vr_render: no cube loaded");
+    if (!ctx->has_tf) return fail(ctx, VR_ERR_STATE, "vr_render: no transfer function set");
+    if (ctx->cams.empty()) return fail(ctx, VR_ERR_STATE, "vr_render: no camera set");
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VR_CK(cudaGetLastError(), "vr_render: pending CUDA error");
+    const int ncams = (int)ctx->cams.size();
+    const int nbatch = (ncams + kMaxLaunchCams - 1) / kMaxLaunchCams;
+    VR_CK(cudaMemsetAsync(ctx->work, 0, sizeof(int) * nbatch, s), "vr_render: scheduler reset");
+    MarchParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.vol = vol_dev(ctx);
+    P.tf.n = (int)ctx->tf.size();
+    for (int i = 0; i < P.tf.n; ++i) P.tf.tab[i] = ctx->tf[(size_t)i];
+    P.tf.vmin = ctx->vmin;
+    P.tf.inv_range = 1.0f / (ctx->vmax - ctx->vmin);
+    P.width = ctx->cams[0].width;
+    P.height = ctx->cams[0].height;
+    P.mode = mode;
+    P.tiles_x = (P.width + kTileW - 1) / kTileW;
+    P.tiles_y = (P.height + kTileH - 1) / kTileH;
+    P.step = ctx->opt.step;
+    P.ert = (float)ctx->opt.ert;
+    P.samples = ctx->sample_counter;
+    const int grid = ctx->num_sms * march_blocks_per_sm(ctx->dtype, mode);
+    const long long img = (long long)P.width * P.height;
+    for (int b = 0; b < nbatch; ++b) {
+        const int c0 = b * kMaxLaunchCams;
+        P.ncams = std::min(kMaxLaunchCams, ncams - c0);
+        for (int i = 0; i < P.ncams; ++i) P.cams[i] = ctx->cams[(size_t)(c0 + i)];
+        P.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)c0 * img;
+        P.out_max = (mode == VR_MIP && out_max) ? out_max + (long long)c0 * img : nullptr;
+        P.work = ctx->work + b;
+        const int tiles = P.tiles_x * P.tiles_y * P.ncams;
+        VR_CK(launch_march(P, ctx->dtype, std::min(grid, tiles), s), "vr_render: march launch");
+    }
+    return VR_OK;
+}
+
+const char* vr_last_error(const vr_ctx* ctx) {
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

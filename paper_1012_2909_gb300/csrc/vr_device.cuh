@@ -1,0 +1,142 @@
+// Device building blocks of the ray caster: camera ray, box interval,
+// brick-local trilinear fetch, transfer-function lookup.
+#pragma once
+
+#include "vr_internal.cuh"
+
+namespace vr {
+
+// Conversion of a stored voxel to FP32 (exact for all three storage types).
+template <typename T> __device__ __forceinline__ float ld_voxel(const T* p);
+template <> __device__ __forceinline__ float ld_voxel<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld_voxel<__half>(const __half* p) {
+    return __half2float(__ldg(p));
+}
+template <> __device__ __forceinline__ float ld_voxel<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+}
+
+// A camera ray in double precision: samples are o + k e, e = step * unit
+// direction, for k in [k0, k1).  The sample range is the half-open slab
+// interval of the box [0,nx]x[0,ny]x[0,nz] with t >= 0 (Sec. 3 renders the
+// same orientation at any output size, so everything is per pixel centre).
+struct Ray {
+    double o[3], e[3];
+    int k0, k1;
+};
+
+__device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, const VolDev& v,
+                                         double step, Ray& r) {
+    const double u = c.l + ((double)px + 0.5) * c.du;
+    const double w = c.t - ((double)py + 0.5) * c.dv;
+    double dd[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (c.type == 0) {
+            r.o[a] = c.eye[a] + u * c.right[a] + w * c.up[a];
+            dd[a] = c.fwd[a];
+        } else {
+            r.o[a] = c.eye[a];
+            dd[a] = c.fwd[a] + u * c.right[a] + w * c.up[a];
+        }
+    }
+    const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+    const double n[3] = {(double)v.nx, (double)v.ny, (double)v.nz};
+    double lo = 0.0, hi = 1e300;
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double d = dd[a] / len;
+        r.e[a] = d * step;
+        if (d == 0.0) {
+            if (r.o[a] < 0.0 || r.o[a] > n[a]) hit = false;
+        } else {
+            const double t1 = (0.0 - r.o[a]) / d, t2 = (n[a] - r.o[a]) / d;
+            lo = fmax(lo, fmin(t1, t2));
+            hi = fmin(hi, fmax(t1, t2));
+        }
+    }
+    r.k0 = r.k1 = 0;
+    if (!hit || !(lo < hi)) return false;
+    const double a = ceil(lo / step), b = ceil(hi / step);
+    r.k0 = (int)fmax(a, 0.0);
+    r.k1 = (int)fmin(b, 2.0e9);
+    return r.k1 > r.k0;
+}
+
+// Brick-local segment state: stored coordinate g = p - brick origin + 1/2,
+// so the lower trilinear corner is floor(g) in slot coordinates (0 = ghost).
+struct Seg {
+    float gx, gy, gz;
+    int n;          // samples in this segment
+    long long base; // element offset of the slot
+};
+
+// Start a segment at sample k: pick the brick holding p_k (any brick whose
+// interior plus a half-voxel margin holds every sample of the segment gives
+// the same values, thanks to the ghost layer), and count the samples that
+// stay inside its interior (at least 1, at most cap).
+__device__ __forceinline__ bool seg_begin(const Ray& r, int k, const VolDev& v, float3 e32,
+                                          int cap, Seg& s) {
+    const double px = fma((double)k, r.e[0], r.o[0]);
+    const double py = fma((double)k, r.e[1], r.o[1]);
+    const double pz = fma((double)k, r.e[2], r.o[2]);
+    int bx = ((int)floor(px)) >> v.log2B, by = ((int)floor(py)) >> v.log2B,
+        bz = ((int)floor(pz)) >> v.log2B;
+    bx = min(max(bx, 0), v.nbx - 1);
+    by = min(max(by, 0), v.nby - 1);
+    bz = min(max(bz, 0), v.nbz - 1);
+    s.gx = (float)(px - (double)(bx << v.log2B)) + 0.5f;
+    s.gy = (float)(py - (double)(by << v.log2B)) + 0.5f;
+    s.gz = (float)(pz - (double)(bz << v.log2B)) + 0.5f;
+    const float hiB = (float)v.B + 0.5f;
+    float m = (float)cap;
+    if (e32.x > 0.f) m = fminf(m, (hiB - s.gx) / e32.x); else if (e32.x < 0.f) m = fminf(m, (0.5f - s.gx) / e32.x);
+    if (e32.y > 0.f) m = fminf(m, (hiB - s.gy) / e32.y); else if (e32.y < 0.f) m = fminf(m, (0.5f - s.gy) / e32.y);
+    if (e32.z > 0.f) m = fminf(m, (hiB - s.gz) / e32.z); else if (e32.z < 0.f) m = fminf(m, (0.5f - s.gz) / e32.z);
+    int n = (int)floorf(m) + 1;
+    n = max(n, 1);
+    n = min(n, min(cap, r.k1 - k));
+    s.n = n;
+    const int slot = v.table[(bz * v.nby + by) * v.nbx + bx];
+    s.base = (long long)slot * v.slot_elems;
+    return slot >= 0;
+}
+
+// Trilinear sample at slot coordinate g (clamped to the slot for safety).
+template <typename T>
+__device__ __forceinline__ float fetch_trilinear(const T* __restrict__ slot, const VolDev& v,
+                                                 float gx, float gy, float gz) {
+    const float B = (float)v.B;
+    gx = fminf(fmaxf(gx, 0.f), B + 0.999f);
+    gy = fminf(fmaxf(gy, 0.f), B + 0.999f);
+    gz = fminf(fmaxf(gz, 0.f), B + 0.999f);
+    const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
+    const float fx = gx - fx0, fy = gy - fy0, fz = gz - fz0;
+    const int ix = (int)fx0, iy = (int)fy0, iz = (int)fz0;
+    const int slab = v.rows * v.pitch;
+    const T* p = slot + (iz * v.rows + iy) * v.pitch + ix;
+    const float c000 = ld_voxel(p), c100 = ld_voxel(p + 1);
+    const float c010 = ld_voxel(p + v.pitch), c110 = ld_voxel(p + v.pitch + 1);
+    const float c001 = ld_voxel(p + slab), c101 = ld_voxel(p + slab + 1);
+    const float c011 = ld_voxel(p + slab + v.pitch), c111 = ld_voxel(p + slab + v.pitch + 1);
+    const float a0 = fmaf(fx, c100 - c000, c000), a1 = fmaf(fx, c110 - c010, c010);
+    const float a2 = fmaf(fx, c101 - c001, c001), a3 = fmaf(fx, c111 - c011, c011);
+    const float b0 = fmaf(fy, a1 - a0, a0), b1 = fmaf(fy, a3 - a2, a2);
+    return fmaf(fz, b1 - b0, b0);
+}
+
+// Node-centred linear lookup of the table in shared memory, clamped.
+__device__ __forceinline__ float4 tf_lookup(const float4* __restrict__ tab, int n, float vmin,
+                                            float inv_range, float val) {
+    float u = (val - vmin) * inv_range;
+    u = fminf(fmaxf(u, 0.f), 1.f);
+    const float x = u * (float)(n - 1);
+    const int i = min((int)x, n - 2);
+    const float w = x - (float)i;
+    const float4 a = tab[i], b = tab[i + 1];
+    return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y),
+                       fmaf(w, b.z - a.z, a.z), fmaf(w, b.w - a.w, a.w));
+}
+
+}  // namespace vr

@@ -1,0 +1,124 @@
+// Image-order ray marcher: one thread per ray, one warp per 8 x 4 pixel tile,
+// tiles handed out by a persistent scheduler (one atomic counter per launch).
+//
+// Per ray (the discretisation of include/vr.h, vr_render): double-precision
+// ray setup and box interval; brick-by-brick traversal, each segment anchored
+// in double precision and stepped in FP32 brick-local coordinates; trilinear
+// fetch from the ghosted brick; transfer-function lookup from shared memory;
+// front-to-back "over" with early termination, or maximum-intensity
+// projection.
+#include "vr_device.cuh"
+
+namespace vr {
+
+namespace {
+
+constexpr int kSegCap = 128;  // samples between double-precision re-anchors
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kMarchThreads)
+k_march(const __grid_constant__ MarchParams P) {
+    __shared__ float4 s_tf[kMaxTF];
+    for (int i = threadIdx.x; i < P.tf.n; i += blockDim.x) s_tf[i] = P.tf.tab[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int tiles_per_cam = P.tiles_x * P.tiles_y;
+    const int total = tiles_per_cam * P.ncams;
+    const T* __restrict__ pool = static_cast<const T*>(P.vol.pool);
+    const float ert = P.ert;
+    unsigned long long my_samples = 0;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(P.work, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        const int cam = item / tiles_per_cam;
+        const int tile = item - cam * tiles_per_cam;
+        const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
+        const int px = tx * kTileW + (lane % kTileW);
+        const int py = ty * kTileH + (lane / kTileW);
+        if (px >= P.width || py >= P.height) continue;  // ragged edge tile; the lane
+                                                        // rejoins at the next shuffle
+        const CamDev& C = P.cams[cam];
+        Ray r;
+        const bool hit = make_ray(C, px, py, P.vol, P.step, r);
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, Tr = 1.f, m = -INFINITY;
+        if (hit) {
+            const float3 e32 = make_float3((float)r.e[0], (float)r.e[1], (float)r.e[2]);
+            int k = r.k0;
+            bool done = false;
+            while (k < r.k1 && !done) {
+                Seg s;
+                seg_begin(r, k, P.vol, e32, kSegCap, s);
+                const T* slot = pool + s.base;
+                for (int j = 0; j < s.n; ++j) {
+                    const float fj = (float)j;
+                    const float v = fetch_trilinear<T>(slot, P.vol, fmaf(fj, e32.x, s.gx),
+                                                       fmaf(fj, e32.y, s.gy),
+                                                       fmaf(fj, e32.z, s.gz));
+                    if (MODE == VR_MIP) {
+                        m = fmaxf(m, v);
+                    } else {
+                        const float4 c = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, v);
+                        const float w = Tr * c.w;
+                        c0 = fmaf(w, c.x, c0);
+                        c1 = fmaf(w, c.y, c1);
+                        c2 = fmaf(w, c.z, c2);
+                        Tr = Tr * (1.f - c.w);
+                        if (1.f - Tr >= ert) {
+                            my_samples += (unsigned long long)(j + 1);
+                            done = true;
+                            break;
+                        }
+                    }
+                }
+                if (!done) my_samples += (unsigned long long)s.n;
+                k += s.n;
+            }
+        }
+        const long long pix = ((long long)cam * P.height + py) * P.width + px;
+        if (MODE == VR_MIP) {
+            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (m > -INFINITY) o = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, m);
+            P.out_rgba[pix] = o;
+            if (P.out_max) P.out_max[pix] = m;
+        } else {
+            P.out_rgba[pix] = make_float4(c0, c1, c2, 1.f - Tr);
+        }
+    }
+    if (P.samples) {
+        unsigned long long s = my_samples;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0 && s) atomicAdd(P.samples, s);
+    }
+}
+
+template <typename T, int MODE>
+void* kernel_ptr() {
+    return reinterpret_cast<void*>(&k_march<T, MODE>);
+}
+
+void* pick(vr_dtype dt, int mode) {
+    if (dt == VR_F32) return mode == VR_MIP ? kernel_ptr<float, VR_MIP>() : kernel_ptr<float, VR_COMPOSITE>();
+    if (dt == VR_F16) return mode == VR_MIP ? kernel_ptr<__half, VR_MIP>() : kernel_ptr<__half, VR_COMPOSITE>();
+    return mode == VR_MIP ? kernel_ptr<__nv_bfloat16, VR_MIP>() : kernel_ptr<__nv_bfloat16, VR_COMPOSITE>();
+}
+
+}  // namespace
+
+int march_blocks_per_sm(vr_dtype dt, int mode) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(dt, mode), kMarchThreads, 0) !=
+        cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_march(const MarchParams& p, vr_dtype dt, int grid, cudaStream_t s) {
+    void* args[] = {const_cast<MarchParams*>(&p)};
+    return cudaLaunchKernel(pick(dt, p.mode), dim3(grid), dim3(kMarchThreads), args, 0, s);
+}
+
+}  // namespace vr
