@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Benchmark of the ray-casting renderer on the survey workload.
+
+Workload (one step = one frame of the orbit, rendered in both modes):
+  1024 x 1024 x 2048 (RA x Dec x channel) synthetic HI-like cube -- noise sigma = 1,
+  2000 seeded Gaussian sources, continuum ripple along the channel axis -- stored as
+  FP16 bricks (128^3 + 1-voxel ghost), perspective 1920 x 1080, 36-frame orbit in 10 deg
+  steps about the Dec axis, step 0.5 voxel; composite with early termination at alpha
+  0.99 (image-order marcher) and MIP (object-order TMA-staged brick pass).
+  The same frames are also timed on the plain FP32 store for comparison.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same workload
+(bounded pixel samples per step) as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "samples/s & ms/frame vs plain FP32 path at stated RGBA error; % HBM roofline"
+WORKLOAD = "survey"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=36)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", default="f16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("vr_brick.cu", "vr_device.cuh", "vr_ff.cuh", "vr_tma.cuh"):
+        with open(os.path.join(ROOT, "paper_1012_2909_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_hash):
+    """DRAM bytes per launch of the brick pass from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "k_brick_mip_survey_f16.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mh = re.search(r"kernel source hash:\s*([0-9a-f]+)", text)
+    mt = re.search(r"dram bytes per launch \(full frame\):\s*([0-9.eE+]+)", text)
+    if not mh or not mt or mh.group(1) != kernel_hash:
+        return None
+    return float(mt.group(1))
+
+
+def load_touch_table():
+    path = os.path.join(ROOT, "tests", "golden", "survey_touched_voxels.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def oracle_sample(vol_rounded, tf, cam, pixels, cfg):
+    """Time the FP64 oracle on the listed pixels, both modes; returns (samples, seconds, results)."""
+    import oracle
+    sc = oracle.Scene(vol_rounded, tf, -1.0, 20.0, cfg["step"], cfg["ert"])
+    t0 = time.perf_counter()
+    rc = oracle.render(sc, cam, "composite", pixels)
+    rm = oracle.render(sc, cam, "mip", pixels)
+    dt = time.perf_counter() - t0
+    return int(rc["nsamples"].sum() + rm["nsamples"].sum()), dt, (rc, rm)
+
+
+def sample_pixels(W, H, n, seed):
+    """n distinct seeded pixels (flat py*W+px) drawn uniformly over the image."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(W * H, size=min(n, W * H), replace=False))
+
+
+# ------------------------------------------------------------------------------ our arm
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import paper_1012_2909_gb300 as vr
+    import synth
+
+    rank, local, world = dist_env()
+    dev = local
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    cfg = synth.CONFIGS[WORKLOAD]
+    p = cfg["cube"]
+    dims = (p["nx"], p["ny"], p["nz"])
+    W, H = cfg["image"]
+    tf = synth.viridis_ramp_tf()
+    cams = synth.orbit(dims, cfg["frames"])
+    t0 = time.time()
+    vol = synth.generate(p)
+    gen_s = time.time() - t0
+
+    def make(storage):
+        r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
+        r.load_cube(vol, storage)
+        r.set_transfer_function(tf, -1.0, 20.0)
+        return r
+
+    rq = make(a.storage)
+    r32 = make("f32")
+    info = rq.cube_info()
+    torch.cuda.synchronize()
+
+    # executed samples per frame and mode (deterministic; counted once, untimed)
+    counter = torch.zeros(1, dtype=torch.int64, device=f"cuda:{dev}")
+    nsamp = {"composite": [], "mip": []}
+    rq.set_path("ray")
+    vr.vr_set_sample_counter(rq.ctx, counter)
+    for c in cams:
+        rq.set_camera(c)
+        for mode in ("composite", "mip"):
+            counter.zero_()
+            rq.render(mode)
+            torch.cuda.synchronize()
+            nsamp[mode].append(int(counter.item()))
+    vr.vr_set_sample_counter(rq.ctx, None)
+    rq.set_path("auto")
+
+    out_c = torch.empty((1, H, W, 4), device=f"cuda:{dev}")
+    out_m = torch.empty((1, H, W, 4), device=f"cuda:{dev}")
+    max_m = torch.empty((1, H, W), device=f"cuda:{dev}")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(a.steps)]
+
+    def step(r, i, kernel_events=None):
+        f = i % len(cams)
+        r.set_camera(cams[f])
+        r.render("composite", out=out_c)
+        if kernel_events is not None:
+            vr.vr_set_kernel_events(r.ctx, *kernel_events)
+        r.render("mip", out=out_m, out_max=max_m, with_max=True)
+        if kernel_events is not None:
+            vr.vr_set_kernel_events(r.ctx, None, None)
+        return nsamp["composite"][f] + nsamp["mip"][f]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+
+    def timed(r, kernel=False):
+        for i in range(a.warmup):
+            step(r, i)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        samples = 0
+        ev[0].record()
+        for i in range(a.steps):
+            samples += step(r, i, kev[i] if kernel else None)
+        ev[1].record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = ev[0].elapsed_time(ev[1])
+        return ms, samples
+
+    with ClockSampler(dev) as clk:
+        ms, samples = timed(rq, kernel=True)
+    clocks = clk.summary()
+    kernel_ms = [kev[i][0].elapsed_time(kev[i][1]) for i in range(a.steps)]
+    ms32, samples32 = timed(r32)
+
+    # max over ranks
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([ms, ms32], device=f"cuda:{dev}")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms, ms32 = float(t[0]), float(t[1])
+        s = torch.tensor([samples], dtype=torch.float64, device=f"cuda:{dev}")
+        tdist.all_reduce(s)
+        total_samples = float(s.item())
+    else:
+        total_samples = float(samples)
+
+    # end to end through the public API: camera from the host in, both images out to
+    # pinned host memory, every step
+    host_c = torch.empty((1, H, W, 4), pin_memory=True)
+    host_m = torch.empty((1, H, W, 4), pin_memory=True)
+    for i in range(a.warmup):
+        step(rq, i)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    esamples = 0
+    for i in range(a.steps):
+        esamples += step(rq, i)
+        host_c.copy_(out_c, non_blocking=True)
+        host_m.copy_(out_m, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([e2e_ms], device=f"cuda:{dev}")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(t[0])
+
+    # roofline of the dominant kernel (the MIP brick pass)
+    touch = load_touch_table()
+    bpv = 2 if a.storage in ("f16", "bf16") else 4
+    frames = [i % len(cams) for i in range(a.steps)]
+    alg_bytes = [touch["mip"][f] * bpv for f in frames]
+    avg_kernel_s = statistics.mean(kernel_ms) / 1e3
+    achieved = statistics.mean(alg_bytes) / avg_kernel_s / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    khash = kernel_source_hash()
+    traffic = profiled_traffic(khash)
+
+    mip_ms = statistics.mean(kernel_ms)
+    res = {
+        "metric": METRIC,
+        "value": total_samples / (ms / 1e3),
+        "unit": "samples/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": ms / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "survey 1024x1024x2048 HI-like cube (2000 sources + ripple), "
+                               f"{a.storage} bricks 128^3+ghost, 1920x1080 perspective, "
+                               "36-frame orbit, step 0.5, composite (ERT 0.99) + MIP per step",
+                   "storage": a.storage, "compute": "f32", "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 ({info['store_bytes'] / 1e9:.2f} GB store)"},
+        "ms_per_frame": {"composite": None, "mip_brick_kernel": mip_ms},
+        "rays_per_s": W * H * 2 * a.steps / (ms / 1e3) * world,
+        "fp32_path": {"ms_per_step": ms32 / a.steps,
+                      "samples_per_s": samples32 / (ms32 / 1e3),
+                      "speedup_of_storage_path": ms32 / ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_brick_mip", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                     "algorithmic_bytes_per_launch": statistics.mean(alg_bytes),
+                     "kernel_source_hash": khash},
+        "e2e": {"value": total_samples / (e2e_ms / 1e3) if world == 1 else
+                float(esamples) * world / (e2e_ms / 1e3),
+                "unit": "samples/s", "h2d_bytes_per_step": 144,
+                "d2h_bytes_per_step": 2 * H * W * 4 * 4},
+        "gpu_launches": 4 * a.steps,
+        "clocks": clocks,
+        "generation_s": gen_s,
+    }
+
+    # CPU baseline: the oracle on a bounded pixel sample of frame 0, rank 0 at N = 1
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        vol_r = oracle.round_storage(vol, a.storage)
+        del vol
+        cam = cams[0]
+        pix = sample_pixels(W, H, 1024, seed=5)
+        s0, t0_, _ = oracle_sample(vol_r, tf, cam, pix, cfg)
+        npx = int(min(W * H, max(1024, 1024 * a.cpu_seconds / max(t0_, 1e-3))))
+        pix = sample_pixels(W, H, npx, seed=6)
+        s1, t1, (rc, rm) = oracle_sample(vol_r, tf, cam, pix, cfg)
+        # parity of the timed frame on the same pixels
+        rq.set_camera(cam)
+        oc = rq.render("composite")
+        om = rq.render("mip")
+        torch.cuda.synchronize()
+        gc = oc[0].cpu().numpy().reshape(-1, 4)[pix]
+        gm = om[0].cpu().numpy().reshape(-1, 4)[pix]
+        ec = np.abs(gc - rc["rgba"]).max(axis=1)
+        em = np.abs(gm - rm["rgba"]).max(axis=1)
+        flagged = rc["flags"] != 0
+        res["cpu_baseline"] = {"value": s1 / t1, "unit": "samples/s", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"{len(pix)} seeded pixels of orbit frame 0, "
+                                         f"composite + MIP, FP64, {t1:.1f} s"}
+        res["rgba_max_abs_err"] = {"composite_unflagged": float(ec[~flagged].max()),
+                                   "composite_flagged_rays": int(flagged.sum()),
+                                   "mip": float(em.max()), "pixels": int(len(pix)),
+                                   "reference": "FP64 oracle on the rounded cube",
+                                   "tolerance": 2e-3 if a.storage != "f32" else 1e-4}
+    # per-mode frame time (composite) from one extra timed pass
+    rq.set_camera(cams[0])
+    e0.record()
+    for _ in range(5):
+        rq.render("composite", out=out_c)
+    e1.record()
+    torch.cuda.synchronize()
+    res["ms_per_frame"]["composite"] = e0.elapsed_time(e1) / 5
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------ reference arm
+def run_reference(a):
+    import numpy as np
+
+    import oracle
+    import synth
+
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    cfg = synth.CONFIGS[WORKLOAD]
+    p = cfg["cube"]
+    dims = (p["nx"], p["ny"], p["nz"])
+    tf = synth.viridis_ramp_tf()
+    cams = synth.orbit(dims, cfg["frames"])
+    vol = oracle.round_storage(synth.generate(p), a.storage)
+    sc = oracle.Scene(vol, tf, -1.0, 20.0, cfg["step"], cfg["ert"])
+    rng = np.random.default_rng(3)
+    W, H = cfg["image"]
+    npix = 384
+
+    def one(i):
+        cam = cams[i % len(cams)]
+        # seeded pixels in the central band of the image, where the cube projects
+        xs = rng.integers(W // 4, 3 * W // 4, npix)
+        ys = rng.integers(H // 8, 7 * H // 8, npix)
+        pix = np.unique(ys * W + xs)
+        rc = oracle.render(sc, cam, "composite", pix)
+        rm = oracle.render(sc, cam, "mip", pix)
+        return int(rc["nsamples"].sum() + rm["nsamples"].sum())
+
+    for i in range(a.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    samples = sum(one(i) for i in range(a.steps))
+    dt = time.perf_counter() - t0
+    v = samples / dt
+    res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s",
+           "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": dt * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "survey 1024x1024x2048 HI-like cube, 1920x1080 perspective "
+                                  "orbit, step 0.5, composite (ERT 0.99) + MIP",
+                      "storage": a.storage},
+           "cpu_baseline": {"value": v, "unit": "samples/s", "cores": os.cpu_count(),
+                            "kind": "oracle",
+                            "sample": f"{npix} seeded pixels per step (central band), "
+                                      "composite + MIP, FP64"},
+           "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -59,6 +59,17 @@ typedef enum { VR_F32 = 0, VR_F16 = 1, VR_BF16 = 2 } vr_dtype;
  * straight RGBA. */
 typedef enum { VR_COMPOSITE = 0, VR_MIP = 1 } vr_mode;
 
+/* Which kernel family renders.
+ * VR_PATH_RAY: image order -- one thread per ray marches brick by brick
+ *   (all modes; early termination).
+ * VR_PATH_BRICK: object order -- the cube is streamed once through shared
+ *   memory in 32^3 cells (TMA-staged) and every ray segment crossing a cell is
+ *   marched there; partial results are folded per pixel.  VR_MIP only; needs
+ *   bricks of at least 32 voxels.
+ * VR_PATH_AUTO (default): VR_PATH_BRICK for VR_MIP when available, else
+ *   VR_PATH_RAY.  Every path computes the same discretisation. */
+typedef enum { VR_PATH_AUTO = 0, VR_PATH_RAY = 1, VR_PATH_BRICK = 2 } vr_path;
+
 /*
  * Camera.  Pixel (px, py), py = 0 the top row, has window coordinates
  *     u = win[0] + (px + 1/2) (win[1] - win[0]) / width
@@ -155,14 +166,30 @@ vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams);
  *   VR_MIP: m = max_k v(p_k); output TF(m) (straight), or 0 with no samples.
  * out_max (DEVICE, ncams x height x width float32, may be NULL) receives m
  * in VR_MIP mode (-inf with no samples); it is ignored in VR_COMPOSITE mode.
+ * out_rgba must be 16-byte aligned and out_max 4-byte aligned.  The brick
+ * path uses out_max (when given) as its per-pixel accumulator.
  * Errors: VR_ERR_STATE if no cube, TF or camera is set; VR_ERR_INVALID_ARG
- * for a NULL out_rgba or bad mode.
+ * for a NULL or misaligned output or bad mode; VR_ERR_INTERNAL if a device-side
+ * wait of an earlier call gave up (reported once, then cleared).
  */
 vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, void* stream);
 
+/* Select the kernel family used by later vr_render calls (see vr_path).
+ * A path that cannot serve a request makes vr_render return
+ * VR_ERR_UNSUPPORTED. */
+vr_status vr_set_path(vr_ctx* ctx, vr_path path);
+
 /* Optional DEVICE counter (uint64) to which vr_render adds the number of
- * samples it executed; NULL switches counting off. */
+ * samples it executed (VR_PATH_RAY only); NULL switches counting off. */
 vr_status vr_set_sample_counter(vr_ctx* ctx, unsigned long long* device_counter);
+
+/* Profiling hook: when both are non-NULL, vr_render records the CUDA events
+ * `start` and `stop` (cudaEvent_t, created by the caller) on its stream just
+ * before the first and just after the last launch of its dominant kernel (the
+ * ray marcher on VR_PATH_RAY, the staged brick pass on VR_PATH_BRICK), so that
+ * cudaEventElapsedTime gives that kernel's device time.  NULL, NULL turns it
+ * off. */
+vr_status vr_set_kernel_events(vr_ctx* ctx, void* start, void* stop);
 
 /* Layout of the loaded cube; VR_ERR_STATE if none is loaded. */
 vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info);

@@ -28,6 +28,8 @@ VR_F32, VR_F16, VR_BF16 = 0, 1, 2
 VR_COMPOSITE, VR_MIP = 0, 1
 DTYPES = {"f32": VR_F32, "f16": VR_F16, "bf16": VR_BF16}
 MODES = {"composite": VR_COMPOSITE, "mip": VR_MIP}
+VR_PATH_AUTO, VR_PATH_RAY, VR_PATH_BRICK = 0, 1, 2
+PATHS = {"auto": VR_PATH_AUTO, "ray": VR_PATH_RAY, "brick": VR_PATH_BRICK}
 
 
 class VrError(RuntimeError):
@@ -69,7 +71,9 @@ SIGNATURES = {
                                                 ctypes.c_float]),
     "vr_set_camera": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "vr_render": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "vr_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
     "vr_set_sample_counter": (ctypes.c_int, [_P, _P]),
+    "vr_set_kernel_events": (ctypes.c_int, [_P, _P, _P]),
     "vr_get_cube_info": (ctypes.c_int, [_P, _P]),
     "vr_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -180,11 +184,27 @@ def vr_render(ctx, mode: str, out_rgba, out_max=None, stream=None, device: int =
     _check(ctx, st, "vr_render")
 
 
+def vr_set_path(ctx, path: str = "auto"):
+    st = load_library().vr_set_path(ctx, PATHS[path])
+    _check(ctx, st, "vr_set_path")
+
+
 def vr_set_sample_counter(ctx, counter=None):
     lib = load_library()
     st = lib.vr_set_sample_counter(ctx, None if counter is None else
                                    ctypes.c_void_p(counter.data_ptr()))
     _check(ctx, st, "vr_set_sample_counter")
+
+
+def vr_set_kernel_events(ctx, start=None, stop=None):
+    """start/stop: torch.cuda.Event(enable_timing=True) (or None, None to turn off)."""
+    lib = load_library()
+    h = (lambda e: None if e is None else ctypes.c_void_p(e.cuda_event))
+    if start is not None:
+        start.record()  # make sure the underlying CUDA events exist
+        stop.record()
+    st = lib.vr_set_kernel_events(ctx, h(start), h(stop))
+    _check(ctx, st, "vr_set_kernel_events")
 
 
 def vr_get_cube_info(ctx) -> dict:
@@ -227,6 +247,9 @@ class Renderer:
             cams = [cams]
         vr_set_camera(self.ctx, cams)
         self.cams = list(cams)
+
+    def set_path(self, path="auto"):
+        vr_set_path(self.ctx, path)
 
     def cube_info(self):
         return vr_get_cube_info(self.ctx)

@@ -10,6 +10,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "vr_internal.cuh"
 
 using namespace vr;
@@ -35,10 +38,20 @@ struct vr_ctx {
     float vmin = 0.f, vmax = 1.f;
     // cameras
     std::vector<CamDev> cams;
+    // brick pass: TMA descriptor of the brick store
+    CUtensorMap tmap;
+    bool has_tmap = false;
+    vr_path path = VR_PATH_AUTO;
     // scratch
     int* work = nullptr;
     int work_slots = 0;
+    int2* krange = nullptr;        // per-pixel sample range of the brick pass
+    unsigned int* enc = nullptr;   // per-pixel running maximum when out_max is NULL
+    long long scratch_pix = 0;
+    int* status_host = nullptr;    // mapped, page-locked device status word
+    int* status_dev = nullptr;
     unsigned long long* sample_counter = nullptr;  // caller-owned
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;  // caller-owned profiling events
 };
 
 namespace {
@@ -99,6 +112,89 @@ VolDev vol_dev(const vr_ctx* c) {
     return v;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// TMA descriptor of the brick store viewed as a 4-D tensor (x, y, z, slot), with
+// the box of one staged cell.  Only bricks of at least 32 voxels have cells.
+bool make_tensor_map(vr_ctx* c) {
+    c->has_tmap = false;
+    int cx, cy, cz, bx, by, bz;
+    brick_cell_dims(c->dtype, &cx, &cy, &cz);
+    brick_box_dims(c->dtype, &bx, &by, &bz);
+    if (c->B < cx || c->B < cy || c->B < cz || bx > c->pitch) return false;
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t e = c->elem;
+    cuuint64_t dims[4] = {(cuuint64_t)c->pitch, (cuuint64_t)c->rows, (cuuint64_t)c->rows,
+                          (cuuint64_t)c->nbx * c->nby * c->nbz};
+    cuuint64_t strides[3] = {c->pitch * e, (cuuint64_t)c->rows * c->pitch * e, (cuuint64_t)c->slot_elems * e};
+    cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUtensorMapDataType dt = c->dtype == VR_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : c->dtype == VR_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = enc(&c->tmap, dt, 4, c->pool, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    c->has_tmap = (r == CUDA_SUCCESS);
+    return c->has_tmap;
+}
+
+void split(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// Float-float camera constants (see CamFF) from a double-precision camera.
+bool cam_ff(const CamDev& d, CamFF& f) {
+    std::memset(&f, 0, sizeof(f));
+    const double* R = d.right;
+    const double* U = d.up;
+    const double* F = d.fwd;
+    double fl = std::sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+    for (int a = 0; a < 3; ++a) {
+        double base = (d.type == 1 ? F[a] : d.eye[a]) + d.l * R[a] + d.t * U[a];
+        split(base, f.base_hi[a], f.base_lo[a]);
+        split(d.du * R[a], f.bx_hi[a], f.bx_lo[a]);
+        split(-d.dv * U[a], f.by_hi[a], f.by_lo[a]);
+        split(d.eye[a], f.org_hi[a], f.org_lo[a]);
+        split(F[a] / fl, f.dir_hi[a], f.dir_lo[a]);
+        f.eye[a] = (float)d.eye[a];
+    }
+    // inverse of the column matrix M = [R U F]
+    const double m[9] = {R[0], U[0], F[0], R[1], U[1], F[1], R[2], U[2], F[2]};
+    const double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                       m[2] * (m[3] * m[7] - m[4] * m[6]);
+    if (!(std::fabs(det) > 1e-12)) return false;
+    const double inv[9] = {(m[4] * m[8] - m[5] * m[7]) / det, (m[2] * m[7] - m[1] * m[8]) / det,
+                           (m[1] * m[5] - m[2] * m[4]) / det, (m[5] * m[6] - m[3] * m[8]) / det,
+                           (m[0] * m[8] - m[2] * m[6]) / det, (m[2] * m[3] - m[0] * m[5]) / det,
+                           (m[3] * m[7] - m[4] * m[6]) / det, (m[1] * m[6] - m[0] * m[7]) / det,
+                           (m[0] * m[4] - m[1] * m[3]) / det};
+    for (int i = 0; i < 9; ++i) f.minv[i] = (float)inv[i];
+    f.l = (float)d.l;
+    f.t = (float)d.t;
+    f.du = (float)d.du;
+    f.dv = (float)d.dv;
+    f.type = d.type;
+    f.width = d.width;
+    f.height = d.height;
+    return true;
+}
+
 bool finite3(const double* v) {
     return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
 }
@@ -152,11 +248,18 @@ vr_status vr_create(vr_ctx** out, int device, const vr_options* opt) {
     DevGuard g(device);
     cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) {
-        ctx->work_slots = 4096 / kMaxLaunchCams + 1;
+        ctx->work_slots = 4096 / kMaxLaunchCams + 4096 + 1;
         e = cudaMalloc(&ctx->work, sizeof(int) * ctx->work_slots);
+    }
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&ctx->status_host), sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *ctx->status_host = 0;
+        e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->status_dev), ctx->status_host, 0);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (ctx->work) cudaFree(ctx->work);
+        if (ctx->status_host) cudaFreeHost(ctx->status_host);
         delete ctx;
         return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
     }
@@ -170,6 +273,9 @@ vr_status vr_destroy(vr_ctx* ctx) {
         DevGuard g(ctx->device);
         free_cube(ctx);
         if (ctx->work) cudaFree(ctx->work);
+        if (ctx->krange) cudaFree(ctx->krange);
+        if (ctx->enc) cudaFree(ctx->enc);
+        if (ctx->status_host) cudaFreeHost(ctx->status_host);
     }
     delete ctx;
     return VR_OK;
@@ -245,6 +351,7 @@ vr_status vr_load_cube(vr_ctx* ctx, const float* src, int src_on_device, int64_t
         VR_CK(cudaFreeAsync(stage, s), "vr_load_cube: staging free");
     }
     VR_CK(cudaStreamSynchronize(s), "vr_load_cube: repack");
+    make_tensor_map(ctx);
     ctx->has_cube = true;
     return VR_OK;
 }
@@ -286,6 +393,8 @@ vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams) {
             return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: non-finite camera");
         if (c.type == 0 && c.fwd[0] == 0.0 && c.fwd[1] == 0.0 && c.fwd[2] == 0.0)
             return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: zero forward vector");
+        if (c.win[1] == c.win[0] || c.win[3] == c.win[2])
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: empty window");
         CamDev& d = out[(size_t)i];
         for (int a = 0; a < 3; ++a) {
             d.eye[a] = c.eye[a];
@@ -314,6 +423,15 @@ vr_status vr_set_sample_counter(vr_ctx* ctx, unsigned long long* device_counter)
     return VR_OK;
 }
 
+vr_status vr_set_kernel_events(vr_ctx* ctx, void* start, void* stop) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if ((start == nullptr) != (stop == nullptr))
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_kernel_events: give both events or neither");
+    ctx->ev_start = static_cast<cudaEvent_t>(start);
+    ctx->ev_stop = static_cast<cudaEvent_t>(stop);
+    return VR_OK;
+}
+
 vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info) {
     if (!ctx || !info) return VR_ERR_INVALID_ARG;
     if (!ctx->has_cube) return VR_ERR_STATE;
@@ -331,28 +449,28 @@ vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info) {
     return VR_OK;
 }
 
-vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, void* stream) {
-    if (!ctx) return VR_ERR_INVALID_ARG;
-    if (mode != VR_COMPOSITE && mode != VR_MIP) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: bad mode");
-    if (!out_rgba) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: out_rgba is NULL");
-    if (reinterpret_cast<uintptr_t>(out_rgba) % 16 || reinterpret_cast<uintptr_t>(out_max) % 4)
-        return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: out_rgba must be 16-byte aligned, out_max 4-byte");
-    if (!ctx->has_cube) return fail(ctx, VR_ERR_STATE, "vr_render: no cube loaded");
-    if (!ctx->has_tf) return fail(ctx, VR_ERR_STATE, "vr_render: no transfer function set");
-    if (ctx->cams.empty()) return fail(ctx, VR_ERR_STATE, "vr_render: no camera set");
-    DevGuard g(ctx->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    VR_CK(cudaGetLastError(), "vr_render: pending CUDA error");
+}  // extern "C"
+
+namespace {
+
+TFDev tf_dev(const vr_ctx* ctx) {
+    TFDev t;
+    std::memset(&t, 0, sizeof(t));
+    t.n = (int)ctx->tf.size();
+    for (int i = 0; i < t.n; ++i) t.tab[i] = ctx->tf[(size_t)i];
+    t.vmin = ctx->vmin;
+    t.inv_range = 1.0f / (ctx->vmax - ctx->vmin);
+    return t;
+}
+
+vr_status render_ray(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, cudaStream_t s) {
     const int ncams = (int)ctx->cams.size();
     const int nbatch = (ncams + kMaxLaunchCams - 1) / kMaxLaunchCams;
     VR_CK(cudaMemsetAsync(ctx->work, 0, sizeof(int) * nbatch, s), "vr_render: scheduler reset");
     MarchParams P;
     std::memset(&P, 0, sizeof(P));
     P.vol = vol_dev(ctx);
-    P.tf.n = (int)ctx->tf.size();
-    for (int i = 0; i < P.tf.n; ++i) P.tf.tab[i] = ctx->tf[(size_t)i];
-    P.tf.vmin = ctx->vmin;
-    P.tf.inv_range = 1.0f / (ctx->vmax - ctx->vmin);
+    P.tf = tf_dev(ctx);
     P.width = ctx->cams[0].width;
     P.height = ctx->cams[0].height;
     P.mode = mode;
@@ -363,6 +481,7 @@ vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, 
     P.samples = ctx->sample_counter;
     const int grid = ctx->num_sms * march_blocks_per_sm(ctx->dtype, mode);
     const long long img = (long long)P.width * P.height;
+    if (ctx->ev_start) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
     for (int b = 0; b < nbatch; ++b) {
         const int c0 = b * kMaxLaunchCams;
         P.ncams = std::min(kMaxLaunchCams, ncams - c0);
@@ -373,7 +492,113 @@ vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, 
         const int tiles = P.tiles_x * P.tiles_y * P.ncams;
         VR_CK(launch_march(P, ctx->dtype, std::min(grid, tiles), s), "vr_render: march launch");
     }
+    if (ctx->ev_stop) VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
     return VR_OK;
+}
+
+vr_status ensure_pixel_scratch(vr_ctx* ctx, long long npix) {
+    if (npix <= ctx->scratch_pix) return VR_OK;
+    if (ctx->krange) cudaFree(ctx->krange);
+    if (ctx->enc) cudaFree(ctx->enc);
+    ctx->krange = nullptr;
+    ctx->enc = nullptr;
+    ctx->scratch_pix = 0;
+    VR_CK(cudaMalloc(&ctx->krange, sizeof(int2) * npix), "vr_render: pixel scratch");
+    VR_CK(cudaMalloc(&ctx->enc, sizeof(unsigned int) * npix), "vr_render: pixel scratch");
+    ctx->scratch_pix = npix;
+    return VR_OK;
+}
+
+// MIP through the brick pass: per camera, pixel set-up (sample ranges, running
+// maxima), the staged brick pass, and the transfer-function finalisation.
+vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStream_t s) {
+    const int W = ctx->cams[0].width, H = ctx->cams[0].height;
+    const long long img = (long long)W * H;
+    vr_status st = ensure_pixel_scratch(ctx, img);
+    if (st != VR_OK) return st;
+    PixelParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.vol = vol_dev(ctx);
+    pp.tf = tf_dev(ctx);
+    pp.step = ctx->opt.step;
+    pp.width = W;
+    pp.height = H;
+    pp.krange = ctx->krange;
+    BrickParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.vol = pp.vol;
+    bp.step = (float)ctx->opt.step;
+    int cx, cy, cz;
+    brick_cell_dims(ctx->dtype, &cx, &cy, &cz);
+    bp.ncells_x = ctx->B / cx;
+    bp.ncells_y = ctx->B / cy;
+    bp.ncells_z = ctx->B / cz;
+    bp.nbricks = ctx->nbx * ctx->nby * ctx->nbz;
+    bp.krange = ctx->krange;
+    bp.status = ctx->status_dev;
+    const int ncams = (int)ctx->cams.size();
+    const int grid = ctx->num_sms;
+    for (int i = 0; i < ncams; ++i) {
+        const CamDev& cd = ctx->cams[(size_t)i];
+        if (!cam_ff(cd, bp.cam))
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: camera basis is singular");
+        pp.cam = cd;
+        pp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)i * img;
+        pp.out_max = out_max ? out_max + (long long)i * img : nullptr;
+        pp.enc = out_max ? reinterpret_cast<unsigned int*>(pp.out_max) : ctx->enc;
+        bp.out_enc = pp.enc;
+        bp.work = ctx->work + kMaxLaunchCams + (i % 4096);
+        VR_CK(cudaMemsetAsync(bp.work, 0, sizeof(int), s), "vr_render: scheduler reset");
+        VR_CK(launch_pixel_setup(pp, s), "vr_render: pixel set-up");
+        if (i == 0 && ctx->ev_start) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
+        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, grid, s), "vr_render: brick pass");
+        if (i == ncams - 1 && ctx->ev_stop) VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
+        VR_CK(launch_mip_finalize(pp, s), "vr_render: finalise");
+    }
+    return VR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vr_status vr_set_path(vr_ctx* ctx, vr_path path) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (path != VR_PATH_AUTO && path != VR_PATH_RAY && path != VR_PATH_BRICK)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_path: unknown path");
+    ctx->path = path;
+    return VR_OK;
+}
+
+vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, void* stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (mode != VR_COMPOSITE && mode != VR_MIP) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: bad mode");
+    if (!out_rgba) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: out_rgba is NULL");
+    if (reinterpret_cast<uintptr_t>(out_rgba) % 16 || reinterpret_cast<uintptr_t>(out_max) % 4)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: out_rgba must be 16-byte aligned, out_max 4-byte");
+    if (!ctx->has_cube) return fail(ctx, VR_ERR_STATE, "vr_render: no cube loaded");
+    if (!ctx->has_tf) return fail(ctx, VR_ERR_STATE, "vr_render: no transfer function set");
+    if (ctx->cams.empty()) return fail(ctx, VR_ERR_STATE, "vr_render: no camera set");
+    if (*ctx->status_host != 0) {
+        const int code = *ctx->status_host;
+        *ctx->status_host = 0;
+        return fail(ctx, VR_ERR_INTERNAL,
+                    "an earlier brick pass stopped: a shared-memory load wait exceeded its bound (status " +
+                        std::to_string(code) + ")");
+    }
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VR_CK(cudaGetLastError(), "vr_render: pending CUDA error");
+    vr_path path = ctx->path;
+    if (path == VR_PATH_AUTO) path = (mode == VR_MIP && ctx->has_tmap) ? VR_PATH_BRICK : VR_PATH_RAY;
+    if (path == VR_PATH_BRICK) {
+        if (mode != VR_MIP)
+            return fail(ctx, VR_ERR_UNSUPPORTED, "vr_render: the brick path renders VR_MIP only");
+        if (!ctx->has_tmap)
+            return fail(ctx, VR_ERR_UNSUPPORTED, "vr_render: the brick path needs bricks of at least 32 voxels");
+        return render_brick_mip(ctx, out_rgba, out_max, s);
+    }
+    return render_ray(ctx, mode, out_rgba, out_max, s);
 }
 
 const char* vr_last_error(const vr_ctx* ctx) {

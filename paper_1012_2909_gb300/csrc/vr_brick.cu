@@ -1,0 +1,484 @@
+// Object-order brick pass for maximum-intensity projection.
+//
+// The paper decomposes a cube larger than one node's memory into pieces that
+// are rendered separately and combined (Abstract, Sec. 1).  On one GPU the
+// same decomposition streams the cube through shared memory exactly once: each
+// CTA takes a brick, stages its cells (32^3 interior voxels + a 1-voxel ghost
+// layer) with TMA into a double buffer, and marches every ray segment that
+// crosses the staged cell, one warp per segment with the lanes on consecutive
+// samples.  Partial maxima are folded with an atomic maximum, which is exact
+// and order-free, so the result equals the per-ray maximum.
+//
+// Sample ownership: along each axis the cell faces are planes X; the sample
+// index where a ray crosses X is kappa(X) = (X - o)/e in FP32, the same number
+// in both cells that share the face, and monotone in X.  The intervals
+// [ceil(kappa(X_i)), ceil(kappa(X_i+1))) therefore partition the ray's samples
+// among the cells (the outermost faces are pushed to infinity), clipped to the
+// ray's [k0, k1) from the double-precision set-up.  Positions are anchored in
+// float-float at the first sample of each segment and stepped in FP32.
+#include <algorithm>
+
+#include "vr_device.cuh"
+#include "vr_ff.cuh"
+#include "vr_tma.cuh"
+
+namespace vr {
+
+namespace {
+
+constexpr int kBrickThreads = 512;
+constexpr int kSegCap = 1024;
+
+template <typename T> struct Cell;
+template <> struct Cell<float> {
+    static constexpr int CX = 32, CY = 32, CZ = 16, BX = 36, BY = 34, BZ = 18;
+};
+template <> struct Cell<__half> {
+    static constexpr int CX = 32, CY = 32, CZ = 32, BX = 40, BY = 34, BZ = 34;
+};
+template <> struct Cell<__nv_bfloat16> {
+    static constexpr int CX = 32, CY = 32, CZ = 32, BX = 40, BY = 34, BZ = 34;
+};
+
+template <typename T> struct TileGeom {
+    static constexpr int BYTES = Cell<T>::BX * Cell<T>::BY * Cell<T>::BZ * (int)sizeof(T);
+    static constexpr int STRIDE = (BYTES + 127) / 128 * 128;
+    static constexpr int SMEM = 2 * STRIDE + kSegCap * 32;
+};
+
+struct SegRec {
+    int pix, n;
+    float gx, gy, gz, ex, ey, ez;
+};
+
+__device__ __forceinline__ unsigned int ord_enc(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord_dec(unsigned int e) {
+    return __uint_as_float((e & 0x80000000u) ? (e & 0x7fffffffu) : ~e);
+}
+
+template <typename T> __device__ __forceinline__ float cvt(T v);
+template <> __device__ __forceinline__ float cvt<float>(float v) { return v; }
+template <> __device__ __forceinline__ float cvt<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float cvt<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+// Trilinear fetch from a staged cell; g in tile coordinates (lower corner
+// floor(g), 0 = ghost).  CLAMP keeps every access inside the tile; without it
+// the caller guarantees 0 <= g < extent + 1 on every axis.
+template <typename T, bool CLAMP>
+__device__ __forceinline__ float tile_fetch(const T* __restrict__ t, float gx, float gy, float gz) {
+    using C = Cell<T>;
+    if (CLAMP) {
+        gx = fminf(fmaxf(gx, 0.f), (float)C::CX + 0.999f);
+        gy = fminf(fmaxf(gy, 0.f), (float)C::CY + 0.999f);
+        gz = fminf(fmaxf(gz, 0.f), (float)C::CZ + 0.999f);
+    }
+    const float x0 = floorf(gx), y0 = floorf(gy), z0 = floorf(gz);
+    const float fx = gx - x0, fy = gy - y0, fz = gz - z0;
+    // linear index formed in FP32 (exact: far below 2^24), one conversion
+    const int i = (int)fmaf(fmaf(z0, (float)C::BY, y0), (float)C::BX, x0);
+    constexpr int SY = C::BX, SZ = C::BX * C::BY;
+    const float c000 = cvt<T>(t[i]), c100 = cvt<T>(t[i + 1]);
+    const float c010 = cvt<T>(t[i + SY]), c110 = cvt<T>(t[i + SY + 1]);
+    const float c001 = cvt<T>(t[i + SZ]), c101 = cvt<T>(t[i + SZ + 1]);
+    const float c011 = cvt<T>(t[i + SZ + SY]), c111 = cvt<T>(t[i + SZ + SY + 1]);
+    const float a0 = fmaf(fx, c100 - c000, c000), a1 = fmaf(fx, c110 - c010, c010);
+    const float a2 = fmaf(fx, c101 - c001, c001), a3 = fmaf(fx, c111 - c011, c011);
+    const float b0 = fmaf(fy, a1 - a0, a0), b1 = fmaf(fy, a3 - a2, a2);
+    return fmaf(fz, b1 - b0, b0);
+}
+
+// Maximum over samples j = lane, lane + 32, ... < n of one segment; two
+// samples per lane per step while the segment is long enough, so that their
+// dependency chains overlap.
+template <typename T, bool CLAMP>
+__device__ __forceinline__ float segment_max(const T* __restrict__ tile, float gx, float gy, float gz,
+                                             float ex, float ey, float ez, int n, int lane) {
+    float m = -INFINITY;
+    int base = 0;
+    for (; base + 32 < n; base += 64) {
+        const float fa = (float)(base + lane);
+        const float fb = fa + 32.f;
+        const float va = tile_fetch<T, CLAMP>(tile, fmaf(fa, ex, gx), fmaf(fa, ey, gy), fmaf(fa, ez, gz));
+        float vb = -INFINITY;
+        if (base + 32 + lane < n)
+            vb = tile_fetch<T, CLAMP>(tile, fmaf(fb, ex, gx), fmaf(fb, ey, gy), fmaf(fb, ez, gz));
+        m = fmaxf(m, fmaxf(va, vb));
+    }
+    if (base < n && base + lane < n) {
+        const float fa = (float)(base + lane);
+        m = fmaxf(m, tile_fetch<T, CLAMP>(tile, fmaf(fa, ex, gx), fmaf(fa, ey, gy), fmaf(fa, ez, gz)));
+    }
+    return m;
+}
+
+// Conservative pixel rectangle of the rays that can cross the box [lo, hi].
+__device__ bool cell_rect(const CamFF& c, float3 lo, float3 hi, int4& r) {
+    float umin = 3e38f, umax = -3e38f, vmin = 3e38f, vmax = -3e38f;
+    bool behind = false;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float wx = ((k & 1) ? hi.x : lo.x) - c.eye[0];
+        const float wy = ((k & 2) ? hi.y : lo.y) - c.eye[1];
+        const float wz = ((k & 4) ? hi.z : lo.z) - c.eye[2];
+        const float a = c.minv[0] * wx + c.minv[1] * wy + c.minv[2] * wz;
+        const float b = c.minv[3] * wx + c.minv[4] * wy + c.minv[5] * wz;
+        float u = a, v = b;
+        if (c.type == 1) {
+            const float z = c.minv[6] * wx + c.minv[7] * wy + c.minv[8] * wz;
+            if (!(z > 1e-3f)) {
+                behind = true;
+                continue;
+            }
+            u = a / z;
+            v = b / z;
+        }
+        umin = fminf(umin, u);
+        umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v);
+        vmax = fmaxf(vmax, v);
+    }
+    int px0, px1, py0, py1;
+    if (behind) {
+        px0 = 0;
+        py0 = 0;
+        px1 = c.width - 1;
+        py1 = c.height - 1;
+    } else {
+        const float xa = (umin - c.l) / c.du - 0.5f, xb = (umax - c.l) / c.du - 0.5f;
+        const float ya = (c.t - vmin) / c.dv - 0.5f, yb = (c.t - vmax) / c.dv - 0.5f;
+        const float fx0 = fminf(xa, xb) - 1.f, fx1 = fmaxf(xa, xb) + 1.f;
+        const float fy0 = fminf(ya, yb) - 1.f, fy1 = fmaxf(ya, yb) + 1.f;
+        if (fx1 < 0.f || fy1 < 0.f || fx0 > (float)c.width || fy0 > (float)c.height) return false;
+        px0 = max(0, (int)floorf(fmaxf(fx0, -1.f)));
+        py0 = max(0, (int)floorf(fmaxf(fy0, -1.f)));
+        px1 = min(c.width - 1, (int)ceilf(fminf(fx1, (float)c.width)));
+        py1 = min(c.height - 1, (int)ceilf(fminf(fy1, (float)c.height)));
+    }
+    r = make_int4(px0, py0, px1, py1);
+    return px0 <= px1 && py0 <= py1;
+}
+
+// Geometry of work unit u = brick * ncells + cell: lower corner, pixel
+// rectangle and TMA coordinates; false if the unit has no work.
+template <typename T>
+__device__ bool unit_geometry(const BrickParams& P, int u, float3& lo, int4& rect, int4& coord) {
+    using C = Cell<T>;
+    const VolDev& v = P.vol;
+    const int ncells = P.ncells_x * P.ncells_y * P.ncells_z;
+    const int brick = u / ncells, cell = u - brick * ncells;
+    const int bx = brick % v.nbx, by = (brick / v.nbx) % v.nby, bz = brick / (v.nbx * v.nby);
+    const int cx = cell % P.ncells_x, cy = (cell / P.ncells_x) % P.ncells_y,
+              cz = cell / (P.ncells_x * P.ncells_y);
+    const int ox = bx * v.B + cx * C::CX, oy = by * v.B + cy * C::CY, oz = bz * v.B + cz * C::CZ;
+    if (ox >= v.nx || oy >= v.ny || oz >= v.nz) return false;
+    lo = make_float3((float)ox, (float)oy, (float)oz);
+    const float3 hi = make_float3((float)(ox + C::CX), (float)(oy + C::CY), (float)(oz + C::CZ));
+    if (!cell_rect(P.cam, lo, hi, rect)) return false;
+    coord = make_int4(cx * C::CX, cy * C::CY, cz * C::CZ, v.table[brick]);
+    return coord.w >= 0;
+}
+
+// Segment of pixel (px, py) inside the cell whose lower corner is lo; false if
+// the ray owns no sample there.
+template <typename T>
+__device__ __forceinline__ bool make_segment(const BrickParams& P, int px, int py, int2 kr,
+                                             float3 lo, SegRec& s) {
+    using C = Cell<T>;
+    const CamFF& c = P.cam;
+    const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+    float o[3], e[3];
+    {
+        float V[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) V[a] = fmaf(sy, c.by_hi[a], fmaf(sx, c.bx_hi[a], c.base_hi[a]));
+        if (c.type == 1) {
+            const float inv = rsqrtf(V[0] * V[0] + V[1] * V[1] + V[2] * V[2]) * P.step;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o[a] = c.org_hi[a];
+                e[a] = V[a] * inv;
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o[a] = V[a];
+                e[a] = c.dir_hi[a] * P.step;
+            }
+        }
+    }
+    const float lo3[3] = {lo.x, lo.y, lo.z};
+    const int ext[3] = {C::CX, C::CY, C::CZ};
+    const int n3[3] = {P.vol.nx, P.vol.ny, P.vol.nz};
+    float klo = -1e9f, khi = 1e9f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const bool first = lo3[a] <= 0.f;
+        const bool last = (int)lo3[a] + ext[a] >= n3[a];
+        const float xl = lo3[a], xh = lo3[a] + (float)ext[a];
+        if (e[a] != 0.f) {
+            const float inv = __frcp_rn(e[a]);
+            const float kl = __fmul_rn(__fsub_rn(xl, o[a]), inv);
+            const float kh = __fmul_rn(__fsub_rn(xh, o[a]), inv);
+            float a0, a1;
+            if (e[a] > 0.f) {
+                a0 = first ? -1e9f : kl;
+                a1 = last ? 1e9f : kh;
+            } else {
+                a0 = last ? -1e9f : kh;
+                a1 = first ? 1e9f : kl;
+            }
+            klo = fmaxf(klo, a0);
+            khi = fminf(khi, a1);
+        } else if (!((first || xl <= o[a]) && (last || o[a] < xh))) {
+            return false;
+        }
+    }
+    klo = fminf(fmaxf(klo, -1e9f), 1e9f);
+    khi = fminf(fmaxf(khi, -1e9f), 1e9f);
+    const int ka = max((int)ceilf(klo), kr.x);
+    const int kb = min((int)ceilf(khi), kr.y);
+    if (ka >= kb) return false;
+    // float-float anchor of sample ka
+    ff E[3], O[3];
+    if (c.type == 1) {
+        ff V[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            V[a] = ff_add(ff_add(ff{c.base_hi[a], c.base_lo[a]}, ff_mul_f(ff{c.bx_hi[a], c.bx_lo[a]}, sx)),
+                          ff_mul_f(ff{c.by_hi[a], c.by_lo[a]}, sy));
+            O[a] = ff{c.org_hi[a], c.org_lo[a]};
+        }
+        const ff n2 = ff_add(ff_add(ff_mul(V[0], V[0]), ff_mul(V[1], V[1])), ff_mul(V[2], V[2]));
+        const ff r = ff_rsqrt(n2);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) E[a] = ff_mul_f(ff_mul(V[a], r), P.step);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            O[a] = ff_add(ff_add(ff{c.base_hi[a], c.base_lo[a]}, ff_mul_f(ff{c.bx_hi[a], c.bx_lo[a]}, sx)),
+                          ff_mul_f(ff{c.by_hi[a], c.by_lo[a]}, sy));
+            E[a] = ff_mul_f(ff{c.dir_hi[a], c.dir_lo[a]}, P.step);
+        }
+    }
+    const float fk = (float)ka;
+    float g[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const ff p = ff_add(O[a], ff_mul_f(E[a], fk));
+        g[a] = __fadd_rn(__fsub_rn(p.hi, lo3[a]), p.lo) + 0.5f;
+    }
+    // Samples lie on the segment between the first and the last one, so if both
+    // are inside [eps, extent + 1 - eps) every sample is; otherwise flag the
+    // segment for the clamped fetch (bit 31 of n).
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float ea = a == 0 ? E[0].hi : (a == 1 ? E[1].hi : E[2].hi);
+        const float gend = fmaf((float)(kb - ka - 1), ea, g[a]);
+        const float top = (float)ext[a] + 1.0f - 1e-3f;
+        inside = inside && g[a] >= 1e-3f && g[a] < top && gend >= 1e-3f && gend < top;
+    }
+    s.pix = py * c.width + px;
+    s.n = (kb - ka) | (inside ? 0 : (int)0x80000000u);
+    s.gx = g[0];
+    s.gy = g[1];
+    s.gz = g[2];
+    s.ex = E[0].hi;
+    s.ey = E[1].hi;
+    s.ez = E[2].hi;
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBrickThreads, 1)
+k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BrickParams P) {
+    using G = TileGeom<T>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    SegRec* segs = reinterpret_cast<SegRec*>(smem + 2 * G::STRIDE);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_unit[2];
+    __shared__ int4 s_rect[2], s_coord[2];
+    __shared__ float3 s_lo[2];
+    __shared__ int s_nseg;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nunits = P.nbricks * P.ncells_x * P.ncells_y * P.ncells_z;
+
+    // thread 0: claim the next unit with work, record it in slot b and start
+    // its TMA load into buffer b
+    auto advance = [&](int b) {
+        int u;
+        for (;;) {
+            u = atomicAdd(P.work, 1);
+            if (u >= nunits) break;
+            float3 lo;
+            int4 rect, coord;
+            if (unit_geometry<T>(P, u, lo, rect, coord)) {
+                s_rect[b] = rect;
+                s_coord[b] = coord;
+                s_lo[b] = lo;
+                break;
+            }
+        }
+        s_unit[b] = u;
+        if (u < nunits) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[b], (uint32_t)G::BYTES);
+            const int4 c = s_coord[b];
+            tma_load_4d(smem + b * G::STRIDE, &tmap, &bar[b], c.x, c.y, c.z, c.w);
+        }
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        advance(0);
+    }
+    __syncthreads();
+
+    uint32_t phase[2] = {0u, 0u};
+    int buf = 0;
+    for (;;) {
+        if (s_unit[buf] >= nunits) break;
+        if (tid == 0) advance(buf ^ 1);  // prefetch the next unit into the other buffer
+        const bool ok = mbar_wait(&bar[buf], phase[buf], P.status);
+        phase[buf] ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            // a load did not complete: wait (bounded) for the other buffer's load,
+            // if one was issued, so that no copy lands in released shared memory
+            if (tid == 0 && s_unit[buf ^ 1] < nunits) mbar_wait(&bar[buf ^ 1], phase[buf ^ 1], nullptr);
+            return;
+        }
+        const T* tile = reinterpret_cast<const T*>(smem + buf * G::STRIDE);
+        const int4 rect = s_rect[buf];
+        const float3 lo = s_lo[buf];
+        const int rw = rect.z - rect.x + 1;
+        const int npx = rw * (rect.w - rect.y + 1);
+        for (int c0 = 0; c0 < npx; c0 += kSegCap) {
+            if (tid == 0) s_nseg = 0;
+            __syncthreads();
+            const int c1 = min(npx, c0 + kSegCap);
+            // phase 1: one thread per pixel of the rectangle -> segment records
+            constexpr int PER = kSegCap / kBrickThreads;
+            int2 kr[PER];
+            int pxv[PER], pyv[PER];
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int i = c0 + tid + q * kBrickThreads;
+                kr[q] = make_int2(0, 0);
+                pyv[q] = rect.y + i / rw;
+                pxv[q] = rect.x + i % rw;
+                if (i < c1) kr[q] = P.krange[pyv[q] * P.cam.width + pxv[q]];
+            }
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                if (kr[q].x >= kr[q].y) continue;
+                SegRec s;
+                if (make_segment<T>(P, pxv[q], pyv[q], kr[q], lo, s)) segs[atomicAdd(&s_nseg, 1)] = s;
+            }
+            __syncthreads();
+            // phase 2: one warp per segment, lanes on consecutive samples
+            const int nseg = s_nseg;
+            for (int si = warp; si < nseg; si += kBrickThreads / 32) {
+                const SegRec s = segs[si];
+                const int n = s.n & 0x7fffffff;
+                float m = s.n >= 0 ? segment_max<T, false>(tile, s.gx, s.gy, s.gz, s.ex, s.ey, s.ez, n, lane)
+                                   : segment_max<T, true>(tile, s.gx, s.gy, s.gz, s.ex, s.ey, s.ez, n, lane);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+                if (lane == 0) atomicMax(&P.out_enc[s.pix], ord_enc(m));
+            }
+            __syncthreads();
+        }
+        buf ^= 1;
+    }
+}
+
+__global__ void k_pixel_setup(const __grid_constant__ PixelParams P) {
+    const int n = P.width * P.height;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        Ray r;
+        make_ray(P.cam, i % P.width, i / P.width, P.vol, P.step, r);
+        P.krange[i] = make_int2(r.k0, r.k1);
+        P.enc[i] = ord_enc(-INFINITY);
+    }
+}
+
+__global__ void k_mip_finalize(const __grid_constant__ PixelParams P) {
+    __shared__ float4 s_tf[kMaxTF];
+    for (int i = threadIdx.x; i < P.tf.n; i += blockDim.x) s_tf[i] = P.tf.tab[i];
+    __syncthreads();
+    const int n = P.width * P.height;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float m = ord_dec(P.enc[i]);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m > -INFINITY) o = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, m);
+        P.out_rgba[i] = o;
+        if (P.out_max) P.out_max[i] = m;
+    }
+}
+
+template <typename T>
+cudaError_t launch_t(const void* tmap, const BrickParams& p, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_brick_mip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TileGeom<T>::SMEM);
+    if (e != cudaSuccess) return e;
+    k_brick_mip<T><<<grid, kBrickThreads, TileGeom<T>::SMEM, s>>>(
+        *static_cast<const CUtensorMap*>(tmap), p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void brick_cell_dims(vr_dtype dt, int* cx, int* cy, int* cz) {
+    if (dt == VR_F32) {
+        *cx = Cell<float>::CX;
+        *cy = Cell<float>::CY;
+        *cz = Cell<float>::CZ;
+    } else {
+        *cx = Cell<__half>::CX;
+        *cy = Cell<__half>::CY;
+        *cz = Cell<__half>::CZ;
+    }
+}
+
+void brick_box_dims(vr_dtype dt, int* bx, int* by, int* bz) {
+    if (dt == VR_F32) {
+        *bx = Cell<float>::BX;
+        *by = Cell<float>::BY;
+        *bz = Cell<float>::BZ;
+    } else {
+        *bx = Cell<__half>::BX;
+        *by = Cell<__half>::BY;
+        *bz = Cell<__half>::BZ;
+    }
+}
+
+cudaError_t launch_pixel_setup(const PixelParams& p, cudaStream_t s) {
+    const int n = p.width * p.height;
+    const int grid = std::min((n + 255) / 256, 152 * 8);
+    k_pixel_setup<<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mip_finalize(const PixelParams& p, cudaStream_t s) {
+    const int n = p.width * p.height;
+    const int grid = std::min((n + 255) / 256, 152 * 8);
+    k_mip_finalize<<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_mip(const void* tmap, const BrickParams& p, vr_dtype dt, int grid,
+                             cudaStream_t s) {
+    if (dt == VR_F32) return launch_t<float>(tmap, p, grid, s);
+    if (dt == VR_F16) return launch_t<__half>(tmap, p, grid, s);
+    return launch_t<__nv_bfloat16>(tmap, p, grid, s);
+}
+
+}  // namespace vr

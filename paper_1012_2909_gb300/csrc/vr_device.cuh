@@ -40,6 +40,25 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, const 
             dd[a] = c.fwd[a] + u * c.right[a] + w * c.up[a];
         }
     }
+    r.k0 = r.k1 = 0;
+    {
+        // FP32 slab test against the box grown by one voxel: a ray that misses the
+        // grown box misses the box whatever the rounding, so it skips the FP64 work.
+        float lo32 = 0.f, hi32 = 3e38f;
+        const float nf[3] = {(float)v.nx, (float)v.ny, (float)v.nz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float o = (float)r.o[a], d = (float)dd[a];
+            if (d == 0.f) {
+                if (o < -1.f || o > nf[a] + 1.f) return false;
+            } else {
+                const float t1 = (-1.f - o) / d, t2 = (nf[a] + 1.f - o) / d;
+                lo32 = fmaxf(lo32, fminf(t1, t2));
+                hi32 = fminf(hi32, fmaxf(t1, t2));
+            }
+        }
+        if (!(lo32 <= hi32 * 1.0001f + 1e-3f)) return false;
+    }
     const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
     const double n[3] = {(double)v.nx, (double)v.ny, (double)v.nz};
     double lo = 0.0, hi = 1e300;
@@ -56,7 +75,6 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, const 
             hi = fmin(hi, fmax(t1, t2));
         }
     }
-    r.k0 = r.k1 = 0;
     if (!hit || !(lo < hi)) return false;
     const double a = ceil(lo / step), b = ceil(hi / step);
     r.k0 = (int)fmax(a, 0.0);

@@ -60,12 +60,61 @@ struct MarchParams {
     int* work;                   // zeroed work counter of this launch
 };
 
+// Float-float camera constants for the brick pass.  With sx = px + 1/2,
+// sy = py + 1/2:  V = base + sx bx + sy by.  Perspective: origin org, direction
+// V / |V|.  Orthographic: origin V, direction dir (constant).  minv is the
+// inverse of the column matrix [right up fwd], used to project cell corners.
+struct CamFF {
+    float base_hi[3], base_lo[3], bx_hi[3], bx_lo[3], by_hi[3], by_lo[3];
+    float org_hi[3], org_lo[3];  // perspective eye
+    float dir_hi[3], dir_lo[3];  // orthographic unit direction
+    float minv[9];               // row-major inverse of [right up fwd]
+    float eye[3];
+    float l, t, du, dv;          // window mapping (FP32 copy, footprints only)
+    int type, width, height, pad;
+};
+
+// Launch parameters of the brick (object-order) pass for one camera.
+struct BrickParams {
+    VolDev vol;
+    CamFF cam;
+    float step;
+    int ncells_x, ncells_y, ncells_z;  // cells per brick along each axis
+    int nbricks;
+    const int2* krange;      // per pixel [k0, k1) from the double-precision set-up
+    unsigned int* out_enc;   // per pixel ordered-int encoding of the running maximum
+    int* work;               // brick counter (zeroed)
+    int* status;             // device status word (0 = ok)
+};
+
+// Per-pixel set-up and finalisation around the brick pass.
+struct PixelParams {
+    VolDev vol;
+    TFDev tf;
+    CamDev cam;
+    double step;
+    int width, height;
+    int2* krange;
+    unsigned int* enc;
+    float4* out_rgba;
+    float* out_max;
+};
+
 // Host-side launchers (defined in the kernel translation units).
 cudaError_t launch_repack(const float* src, long long src_z0, long long src_planes, int bz,
                           const VolDev& v, vr_dtype dt, void* pool, unsigned int* minmax,
                           cudaStream_t s);
 cudaError_t launch_march(const MarchParams& p, vr_dtype dt, int grid, cudaStream_t s);
 int march_blocks_per_sm(vr_dtype dt, int mode);
+cudaError_t launch_pixel_setup(const PixelParams& p, cudaStream_t s);
+cudaError_t launch_mip_finalize(const PixelParams& p, cudaStream_t s);
+cudaError_t launch_brick_mip(const void* tmap, const BrickParams& p, vr_dtype dt, int grid,
+                             cudaStream_t s);
+// Cell (staging unit) edge lengths for a storage type; the brick edge must be a
+// multiple of each.
+void brick_cell_dims(vr_dtype dt, int* cx, int* cy, int* cz);
+// TMA box of one cell (cell + 2 ghost, x padded to 16 bytes), in elements.
+void brick_box_dims(vr_dtype dt, int* bx, int* by, int* bz);
 constexpr int kMarchThreads = 128;
 
 inline int ilog2(int v) {

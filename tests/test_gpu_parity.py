@@ -24,8 +24,9 @@ def vr():
 
 
 def _render(vr, vol, tf, cams, mode, storage="f32", brick=128, step=0.5, ert=0.99, vmin=-1.0,
-            vmax=20.0):
+            vmax=20.0, path="auto"):
     r = vr.Renderer(0, brick=brick, step=step, ert=ert)
+    r.set_path(path)
     r.load_cube(vol, storage)
     r.set_transfer_function(tf, vmin, vmax)
     r.set_camera(cams)
@@ -195,6 +196,41 @@ def test_status_codes(vr):
     r.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("brick", [32, 64])
+def test_brick_path_mip(vr, storage, brick):
+    """Object-order MIP (TMA-staged cells) on ragged cubes, several views, both camera types."""
+    for dims in ((96, 80, 72), (45, 37, 29), (33, 70, 130)):
+        p = synth.cube_params(*dims, seed=sum(dims), nsrc=8, ripple=True, ripple_period=32.0)
+        vol = synth.generate(p)
+        tf = synth.viridis_ramp_tf()
+        cams = [synth.orbit_view(dims, az, 61, 47) for az in (0.0, 33.0, 90.0, 200.0)]
+        cams += [synth.ortho_view(dims, 61, 47, rx_deg=15.0, ry_deg=-40.0),
+                 synth.axis_view(dims, 61, 47, plane_offset=-3.3) | {"width": 61, "height": 47},
+                 synth.look_at(dims, (0.2, 0.5, 1.0), 61, 47, dist_factor=0.35)]  # eye inside
+        sc = oracle.Scene(oracle.round_storage(vol, storage), tf, -1.0, 20.0, 0.5, 0.99)
+        img, mx = _render(vr, vol, tf, cams, "mip", storage=storage, brick=brick, path="brick")
+        for i, c in enumerate(cams):
+            compare(img[i].reshape(-1, 4), sc, c, "mip", tol=1e-4, gpu_max=mx[i], max_tol=2e-3)
+
+
+def test_brick_path_rejects_composite_and_small_bricks(vr):
+    vol = np.zeros((40, 40, 40), np.float32)
+    r = vr.Renderer(0, brick=16)
+    r.load_cube(vol)
+    r.set_transfer_function(synth.viridis_ramp_tf(), 0.0, 1.0)
+    r.set_camera(synth.orbit_view((40, 40, 40), 0.0, 8, 8))
+    r.set_path("brick")
+    for mode in ("mip", "composite"):
+        with pytest.raises(vr.VrError) as e:
+            r.render(mode)
+        assert e.value.status == vr.VR_ERR_UNSUPPORTED
+    r.set_path("auto")
+    r.render("mip")  # falls back to the ray path
+    torch.cuda.synchronize()
+    r.close()
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_survey_workload_sampled_pixels(vr, storage):
     """Full-size 1024 x 1024 x 2048 cube (2000 sources + ripple), perspective 1920 x 1080,
@@ -214,7 +250,8 @@ def test_survey_workload_sampled_pixels(vr, storage):
     sc = oracle.Scene(ref_vol, tf, -1.0, 20.0, 0.5, 0.99)
     rng = np.random.default_rng(2024)
     pix = rng.choice(1920 * 1080, 4096, replace=False)
-    for mode in ("composite", "mip"):
+    for mode, path in (("composite", "ray"), ("mip", "ray"), ("mip", "brick")):
+        r.set_path(path)
         out, mx = r.render(mode, with_max=True)
         torch.cuda.synchronize()
         img = out.cpu().numpy().reshape(2, -1, 4)
@@ -222,5 +259,5 @@ def test_survey_workload_sampled_pixels(vr, storage):
         for i, c in enumerate(cams):
             st = compare(img[i][pix], sc, c, mode, pixels=pix, tol=1e-4,
                          gpu_max=mxs[i][pix] if mode == "mip" else None, max_tol=2e-3)
-            print(storage, mode, i, st)
+            print(storage, mode, path, i, st)
     r.close()
