@@ -191,6 +191,36 @@ vr_status vr_set_sample_counter(vr_ctx* ctx, unsigned long long* device_counter)
  * off. */
 vr_status vr_set_kernel_events(vr_ctx* ctx, void* start, void* stop);
 
+/*
+ * Allocation-free MIP render.  The paper has no counterpart: this is a
+ * service to callers of this library that cannot allocate device memory while
+ * they render -- code that records work while a stream is being captured into
+ * a CUDA graph (an allocation there fails the capture), code that must not
+ * trigger the device-wide synchronisation cudaMalloc can imply, and programs
+ * whose device memory is managed by another allocator.  vr_render's brick path
+ * allocates its per-pixel scratch on first use of a larger image; this call
+ * instead takes its scratch (per-pixel sample ranges, per-pixel running
+ * maxima, the work counter) from one fixed array compiled into the library,
+ * VR_NOALLOC_MAX_PIXELS * 12 bytes + 256 (24 MiB), present on every device
+ * that loads the library until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ * Result: the same as vr_render(ctx, VR_MIP, out_rgba, out_max, stream) on
+ * VR_PATH_BRICK (same outputs, layouts and alignment rules).
+ * Limits: every camera must have at most VR_NOALLOC_MAX_PIXELS pixels
+ * (width * height), else VR_ERR_INVALID_ARG; bricks of at least 32 voxels,
+ * else VR_ERR_UNSUPPORTED.
+ * Set-up: the first call on each device looks up the device address of the
+ * scratch array (with that device current); make that first call before any
+ * stream capture.
+ * Sharing: every call on a device uses the same scratch array, which keeps the
+ * last call's contents; each call rewrites what it reads before reading it.
+ * Calls whose GPU work overlaps (on different streams, or from several
+ * threads, without ordering between them) race on the array and produce wrong
+ * images: order them on one stream or synchronise between them.
+ */
+#define VR_NOALLOC_MAX_PIXELS (1 << 21)
+vr_status vr_render_mip_noalloc(vr_ctx* ctx, float* out_rgba, float* out_max, void* stream);
+
 /* Layout of the loaded cube; VR_ERR_STATE if none is loaded. */
 vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info);
 

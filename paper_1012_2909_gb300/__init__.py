@@ -74,6 +74,7 @@ SIGNATURES = {
     "vr_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
     "vr_set_sample_counter": (ctypes.c_int, [_P, _P]),
     "vr_set_kernel_events": (ctypes.c_int, [_P, _P, _P]),
+    "vr_render_mip_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "vr_get_cube_info": (ctypes.c_int, [_P, _P]),
     "vr_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -182,6 +183,19 @@ def vr_render(ctx, mode: str, out_rgba, out_max=None, stream=None, device: int =
                        None if out_max is None else ctypes.c_void_p(out_max.data_ptr()),
                        _stream_handle(stream, device))
     _check(ctx, st, "vr_render")
+
+
+VR_NOALLOC_MAX_PIXELS = 1 << 21
+
+
+def vr_render_mip_noalloc(ctx, out_rgba, out_max=None, stream=None, device: int = 0):
+    """MIP into caller-provided device tensors with no device allocation by the library
+    (scratch is a fixed array inside libvr.so; see include/vr.h)."""
+    lib = load_library()
+    st = lib.vr_render_mip_noalloc(ctx, ctypes.c_void_p(out_rgba.data_ptr()),
+                                   None if out_max is None else ctypes.c_void_p(out_max.data_ptr()),
+                                   _stream_handle(stream, device))
+    _check(ctx, st, "vr_render_mip_noalloc")
 
 
 def vr_set_path(ctx, path: str = "auto"):

@@ -560,6 +560,83 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
 
 }  // namespace
 
+namespace vr {
+
+// Checks shared by allocation-free callers of the brick-path MIP: context
+// state, output alignment, a usable brick store.  On success returns the
+// context's device and the pixel count of one camera.
+vr_status brick_mip_precheck(vr_ctx* ctx, float* out_rgba, float* out_max, int* device,
+                             long long* pixels) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!out_rgba) return fail(ctx, VR_ERR_INVALID_ARG, "out_rgba is NULL");
+    if (reinterpret_cast<uintptr_t>(out_rgba) % 16 || reinterpret_cast<uintptr_t>(out_max) % 4)
+        return fail(ctx, VR_ERR_INVALID_ARG, "out_rgba must be 16-byte aligned, out_max 4-byte");
+    if (!ctx->has_cube) return fail(ctx, VR_ERR_STATE, "no cube loaded");
+    if (!ctx->has_tf) return fail(ctx, VR_ERR_STATE, "no transfer function set");
+    if (ctx->cams.empty()) return fail(ctx, VR_ERR_STATE, "no camera set");
+    if (!ctx->has_tmap)
+        return fail(ctx, VR_ERR_UNSUPPORTED, "the brick pass needs bricks of at least 32 voxels");
+    if (*ctx->status_host != 0) {
+        const int code = *ctx->status_host;
+        *ctx->status_host = 0;
+        return fail(ctx, VR_ERR_INTERNAL,
+                    "an earlier brick pass stopped: a shared-memory load wait exceeded its bound (status " +
+                        std::to_string(code) + ")");
+    }
+    *device = ctx->device;
+    *pixels = (long long)ctx->cams[0].width * ctx->cams[0].height;
+    return VR_OK;
+}
+
+vr_status set_error(vr_ctx* ctx, vr_status s, const char* msg) { return fail(ctx, s, msg); }
+
+// Brick-path MIP of every camera with caller-provided scratch: krange and enc
+// hold one camera's pixels, work one int.  Allocates nothing.
+vr_status brick_mip_with_scratch(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStream_t s,
+                                 int2* krange, unsigned int* enc, int* work) {
+    const int W = ctx->cams[0].width, H = ctx->cams[0].height;
+    const long long img = (long long)W * H;
+    VR_CK(cudaGetLastError(), "pending CUDA error");
+    PixelParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.vol = vol_dev(ctx);
+    pp.tf = tf_dev(ctx);
+    pp.step = ctx->opt.step;
+    pp.width = W;
+    pp.height = H;
+    pp.krange = krange;
+    BrickParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.vol = pp.vol;
+    bp.step = (float)ctx->opt.step;
+    int cx, cy, cz;
+    brick_cell_dims(ctx->dtype, &cx, &cy, &cz);
+    bp.ncells_x = ctx->B / cx;
+    bp.ncells_y = ctx->B / cy;
+    bp.ncells_z = ctx->B / cz;
+    bp.nbricks = ctx->nbx * ctx->nby * ctx->nbz;
+    bp.krange = krange;
+    bp.status = ctx->status_dev;
+    bp.work = work;
+    const int ncams = (int)ctx->cams.size();
+    for (int i = 0; i < ncams; ++i) {
+        if (!cam_ff(ctx->cams[(size_t)i], bp.cam))
+            return fail(ctx, VR_ERR_INVALID_ARG, "camera basis is singular");
+        pp.cam = ctx->cams[(size_t)i];
+        pp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)i * img;
+        pp.out_max = out_max ? out_max + (long long)i * img : nullptr;
+        pp.enc = enc;
+        bp.out_enc = enc;
+        VR_CK(cudaMemsetAsync(work, 0, sizeof(int), s), "scheduler reset");
+        VR_CK(launch_pixel_setup(pp, s), "pixel set-up");
+        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, ctx->num_sms, s), "brick pass");
+        VR_CK(launch_mip_finalize(pp, s), "finalise");
+    }
+    return VR_OK;
+}
+
+}  // namespace vr
+
 extern "C" {
 
 vr_status vr_set_path(vr_ctx* ctx, vr_path path) {

@@ -116,6 +116,12 @@ void brick_cell_dims(vr_dtype dt, int* cx, int* cy, int* cz);
 // TMA box of one cell (cell + 2 ghost, x padded to 16 bytes), in elements.
 void brick_box_dims(vr_dtype dt, int* bx, int* by, int* bz);
 constexpr int kMarchThreads = 128;
+// Brick-path MIP pieces used by the allocation-free entry point (vr_api.cu).
+vr_status brick_mip_precheck(vr_ctx* ctx, float* out_rgba, float* out_max, int* device,
+                             long long* pixels);
+vr_status brick_mip_with_scratch(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStream_t s,
+                                 int2* krange, unsigned int* enc, int* work);
+vr_status set_error(vr_ctx* ctx, vr_status s, const char* msg);
 
 inline int ilog2(int v) {
     int r = 0;
