@@ -39,6 +39,11 @@ def parse():
     ap.add_argument("--storage", default="f16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile", choices=["mip", "composite", "both"], default=None,
+                    help="only render --warmup + --steps orbit frames (for ncu); no timing legs")
+    ap.add_argument("--cube", default=None,
+                    help="NX,NY,NZ: override the cube size (same source density) for small captures")
+    ap.add_argument("--frame", type=int, default=None, help="with --profile: render this frame only")
     return ap.parse_args()
 
 
@@ -432,8 +437,49 @@ def run_reference(a):
     print(json.dumps(res), flush=True)
 
 
+def run_profile(a):
+    """Render frames of the workload and nothing else, so that a profiler sees only the
+    renderer's kernels (used by the commands in profiles/)."""
+    import torch
+
+    import paper_1012_2909_gb300 as vr
+    import synth
+
+    cfg = synth.CONFIGS[WORKLOAD]
+    p = dict(cfg["cube"])
+    if a.cube:
+        nx, ny, nz = (int(v) for v in a.cube.split(","))
+        scale = nx * ny * nz / (p["nx"] * p["ny"] * p["nz"])
+        p.update(nx=nx, ny=ny, nz=nz, nsrc=max(1, int(round(p["nsrc"] * scale))))
+    dims = (p["nx"], p["ny"], p["nz"])
+    vol = synth.generate(p)
+    r = vr.Renderer(0, brick=128, step=cfg["step"], ert=cfg["ert"])
+    r.load_cube(vol, a.storage)
+    del vol
+    r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
+    cams = synth.orbit(dims, cfg["frames"])
+    modes = ["composite", "mip"] if a.profile == "both" else [a.profile]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = a.warmup + a.steps
+    for i in range(n):
+        if i == a.warmup:
+            torch.cuda.synchronize()
+            e0.record()
+        r.set_camera(cams[a.frame if a.frame is not None else i % len(cams)])
+        for m in modes:
+            r.render(m)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": a.profile, "cube": dims, "storage": a.storage, "frames": a.steps,
+                      "ms_per_frame": e0.elapsed_time(e1) / max(a.steps, 1)}))
+    r.close()
+
+
 def main():
     a = parse()
+    if a.profile:
+        run_profile(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

@@ -202,8 +202,9 @@ vr_status vr_set_kernel_events(vr_ctx* ctx, void* start, void* stop);
  * instead takes its scratch (per-pixel sample ranges, per-pixel running
  * maxima, the work counter) from one fixed array compiled into the library,
  * VR_NOALLOC_MAX_PIXELS * 12 bytes + 256 (24 MiB), present on every device
- * that loads the library until the process exits.  It calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * that loads the library until the process exits; the per-view cell list it
+ * also needs belongs to the context and is allocated once by vr_load_cube.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
  * Result: the same as vr_render(ctx, VR_MIP, out_rgba, out_max, stream) on
  * VR_PATH_BRICK (same outputs, layouts and alignment rules).
  * Limits: every camera must have at most VR_NOALLOC_MAX_PIXELS pixels

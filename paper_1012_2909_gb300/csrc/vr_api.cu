@@ -32,6 +32,7 @@ struct vr_ctx {
     void* pool = nullptr;
     int* table = nullptr;
     unsigned int* minmax = nullptr;
+    void* cells = nullptr;   // brick-pass cell list of the current view
     // transfer function
     bool has_tf = false;
     std::vector<float4> tf;
@@ -88,9 +89,11 @@ void free_cube(vr_ctx* c) {
     if (c->pool) cudaFree(c->pool);
     if (c->table) cudaFree(c->table);
     if (c->minmax) cudaFree(c->minmax);
+    if (c->cells) cudaFree(c->cells);
     c->pool = nullptr;
     c->table = nullptr;
     c->minmax = nullptr;
+    c->cells = nullptr;
     c->has_cube = false;
 }
 
@@ -351,7 +354,12 @@ vr_status vr_load_cube(vr_ctx* ctx, const float* src, int src_on_device, int64_t
         VR_CK(cudaFreeAsync(stage, s), "vr_load_cube: staging free");
     }
     VR_CK(cudaStreamSynchronize(s), "vr_load_cube: repack");
-    make_tensor_map(ctx);
+    if (make_tensor_map(ctx)) {
+        int cx, cy, cz;
+        brick_cell_dims(ctx->dtype, &cx, &cy, &cz);
+        const long long units = nbricks * (long long)(B / cx) * (B / cy) * (B / cz);
+        VR_CK(cudaMalloc(&ctx->cells, brick_cells_bytes(units)), "vr_load_cube: cell list allocation");
+    }
     ctx->has_cube = true;
     return VR_OK;
 }
@@ -537,7 +545,7 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
     bp.krange = ctx->krange;
     bp.status = ctx->status_dev;
     const int ncams = (int)ctx->cams.size();
-    const int grid = ctx->num_sms;
+    const int grid = 2 * ctx->num_sms;
     for (int i = 0; i < ncams; ++i) {
         const CamDev& cd = ctx->cams[(size_t)i];
         if (!cam_ff(cd, bp.cam))
@@ -551,7 +559,7 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
         VR_CK(cudaMemsetAsync(bp.work, 0, sizeof(int), s), "vr_render: scheduler reset");
         VR_CK(launch_pixel_setup(pp, s), "vr_render: pixel set-up");
         if (i == 0 && ctx->ev_start) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
-        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, grid, s), "vr_render: brick pass");
+        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, grid, ctx->cells, s), "vr_render: brick pass");
         if (i == ncams - 1 && ctx->ev_stop) VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
         VR_CK(launch_mip_finalize(pp, s), "vr_render: finalise");
     }
@@ -629,7 +637,7 @@ vr_status brick_mip_with_scratch(vr_ctx* ctx, float* out_rgba, float* out_max, c
         bp.out_enc = enc;
         VR_CK(cudaMemsetAsync(work, 0, sizeof(int), s), "scheduler reset");
         VR_CK(launch_pixel_setup(pp, s), "pixel set-up");
-        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, ctx->num_sms, s), "brick pass");
+        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, 2 * ctx->num_sms, ctx->cells, s), "brick pass");
         VR_CK(launch_mip_finalize(pp, s), "finalise");
     }
     return VR_OK;

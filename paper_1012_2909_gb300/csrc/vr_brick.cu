@@ -26,8 +26,16 @@ namespace vr {
 
 namespace {
 
-constexpr int kBrickThreads = 512;
-constexpr int kSegCap = 1024;
+constexpr int kBrickThreads = 256;  // two CTAs per SM
+constexpr int kSegCap = 512;        // segment records per chunk
+#ifndef VR_BRICK_GROUP
+#define VR_BRICK_GROUP 8
+#endif
+constexpr int kGroup = VR_BRICK_GROUP;  // lanes per segment in the march
+#ifndef VR_BRICK_UNROLL
+#define VR_BRICK_UNROLL 1
+#endif
+constexpr int kUnroll = VR_BRICK_UNROLL;  // samples per lane per step
 
 template <typename T> struct Cell;
 template <> struct Cell<float> {
@@ -43,7 +51,7 @@ template <> struct Cell<__nv_bfloat16> {
 template <typename T> struct TileGeom {
     static constexpr int BYTES = Cell<T>::BX * Cell<T>::BY * Cell<T>::BZ * (int)sizeof(T);
     static constexpr int STRIDE = (BYTES + 127) / 128 * 128;
-    static constexpr int SMEM = 2 * STRIDE + kSegCap * 32;
+    static constexpr int SMEM = STRIDE + kSegCap * 32;
 };
 
 struct SegRec {
@@ -79,7 +87,6 @@ __device__ __forceinline__ float tile_fetch(const T* __restrict__ t, float gx, f
     }
     const float x0 = floorf(gx), y0 = floorf(gy), z0 = floorf(gz);
     const float fx = gx - x0, fy = gy - y0, fz = gz - z0;
-    // linear index formed in FP32 (exact: far below 2^24), one conversion
     const int i = (int)fmaf(fmaf(z0, (float)C::BY, y0), (float)C::BX, x0);
     constexpr int SY = C::BX, SZ = C::BX * C::BY;
     const float c000 = cvt<T>(t[i]), c100 = cvt<T>(t[i + 1]);
@@ -92,29 +99,6 @@ __device__ __forceinline__ float tile_fetch(const T* __restrict__ t, float gx, f
     return fmaf(fz, b1 - b0, b0);
 }
 
-// Maximum over samples j = lane, lane + 32, ... < n of one segment; two
-// samples per lane per step while the segment is long enough, so that their
-// dependency chains overlap.
-template <typename T, bool CLAMP>
-__device__ __forceinline__ float segment_max(const T* __restrict__ tile, float gx, float gy, float gz,
-                                             float ex, float ey, float ez, int n, int lane) {
-    float m = -INFINITY;
-    int base = 0;
-    for (; base + 32 < n; base += 64) {
-        const float fa = (float)(base + lane);
-        const float fb = fa + 32.f;
-        const float va = tile_fetch<T, CLAMP>(tile, fmaf(fa, ex, gx), fmaf(fa, ey, gy), fmaf(fa, ez, gz));
-        float vb = -INFINITY;
-        if (base + 32 + lane < n)
-            vb = tile_fetch<T, CLAMP>(tile, fmaf(fb, ex, gx), fmaf(fb, ey, gy), fmaf(fb, ez, gz));
-        m = fmaxf(m, fmaxf(va, vb));
-    }
-    if (base < n && base + lane < n) {
-        const float fa = (float)(base + lane);
-        m = fmaxf(m, tile_fetch<T, CLAMP>(tile, fmaf(fa, ex, gx), fmaf(fa, ey, gy), fmaf(fa, ez, gz)));
-    }
-    return m;
-}
 
 // Conservative pixel rectangle of the rays that can cross the box [lo, hi].
 __device__ bool cell_rect(const CamFF& c, float3 lo, float3 hi, int4& r) {
@@ -221,7 +205,8 @@ __device__ __forceinline__ bool make_segment(const BrickParams& P, int px, int p
         const bool last = (int)lo3[a] + ext[a] >= n3[a];
         const float xl = lo3[a], xh = lo3[a] + (float)ext[a];
         if (e[a] != 0.f) {
-            const float inv = __frcp_rn(e[a]);
+            const float inv = __fdividef(1.0f, e[a]);  // any fixed reciprocal keeps kappa
+                                                       // deterministic and monotone in X
             const float kl = __fmul_rn(__fsub_rn(xl, o[a]), inv);
             const float kh = __fmul_rn(__fsub_rn(xh, o[a]), inv);
             float a0, a1;
@@ -294,109 +279,188 @@ __device__ __forceinline__ bool make_segment(const BrickParams& P, int px, int p
     return true;
 }
 
+struct CellDesc {
+    float4 lo;    // lower corner (world voxels)
+    int4 rect;    // pixel rectangle px0, py0, px1, py1 (inclusive)
+    int4 coord;   // TMA coordinates x, y, z (slot elements), slot
+};
+
+// Compacted list of the cells that some pixel of this view can reach, in
+// roughly linear cell order (warp-aggregated appends), so that neighbouring
+// cells -- which share ghost voxels through L2 -- run close in time.
 template <typename T>
-__global__ void __launch_bounds__(kBrickThreads, 1)
-k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BrickParams P) {
+__global__ void k_cell_list(const __grid_constant__ BrickParams P, CellDesc* __restrict__ list,
+                            int* __restrict__ count) {
+    const int nunits = P.nbricks * P.ncells_x * P.ncells_y * P.ncells_z;
+    const int lane = threadIdx.x & 31;
+    for (int u0 = blockIdx.x * blockDim.x; u0 < nunits; u0 += gridDim.x * blockDim.x) {
+        const int u = u0 + threadIdx.x;
+        float3 lo;
+        int4 rect, coord;
+        const bool ok = u < nunits && unit_geometry<T>(P, u, lo, rect, coord);
+        const unsigned int m = __ballot_sync(0xffffffffu, ok);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) {
+            CellDesc d;
+            d.lo = make_float4(lo.x, lo.y, lo.z, 0.f);
+            d.rect = rect;
+            d.coord = coord;
+            list[base + __popc(m & ((1u << lane) - 1u))] = d;
+        }
+    }
+}
+
+// One chunk of a cell's pixel rectangle -> segment records (phase 1).
+template <typename T>
+__device__ __forceinline__ void build_segments(const BrickParams& P, const CellDesc& d, int c0,
+                                               SegRec* segs, int* cnt, int tid) {
+    const int4 rect = d.rect;
+    const int rw = rect.z - rect.x + 1;
+    const int npx = rw * (rect.w - rect.y + 1);
+    const int c1 = min(npx, c0 + kSegCap);
+    const float3 lo = make_float3(d.lo.x, d.lo.y, d.lo.z);
+    constexpr int PER = kSegCap / kBrickThreads;
+    int2 kr[PER];
+    int pxv[PER], pyv[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = c0 + tid + q * kBrickThreads;
+        kr[q] = make_int2(0, 0);
+        pyv[q] = rect.y + i / rw;
+        pxv[q] = rect.x + i % rw;
+        if (i < c1) kr[q] = P.krange[pyv[q] * P.cam.width + pxv[q]];
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        if (kr[q].x >= kr[q].y) continue;
+        SegRec s;
+        if (make_segment<T>(P, pxv[q], pyv[q], kr[q], lo, s)) segs[atomicAdd(cnt, 1)] = s;
+    }
+}
+
+// Phase 2: groups of G lanes per segment record (32/G records per warp at a
+// time, consecutive records -- neighbouring pixels, similar lengths), lane r of
+// a group on samples j = r, r + G, ...; U samples per lane per step so that
+// their dependency chains overlap.  Lanes past the end of their segment
+// re-sample its last sample: a maximum is unchanged by repeats, and the step
+// stays free of divergent branches.  The maximum of a group is folded with
+// redux.sync on its ordered-int encoding.
+template <typename T, int G, int U, bool CLAMP>
+__device__ __forceinline__ float group_max(const T* __restrict__ tile, const SegRec& s, int n, int r,
+                                           int iters) {
+    float m = -INFINITY;
+    const int last = n - 1;
+    for (int it = 0; it < iters; ++it) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float f = (float)min(it * U * G + u * G + r, last);
+            v[u] = tile_fetch<T, CLAMP>(tile, fmaf(f, s.ex, s.gx), fmaf(f, s.ey, s.gy), fmaf(f, s.ez, s.gz));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) m = fmaxf(m, v[u]);
+    }
+    return m;
+}
+
+template <typename T, int G, int U>
+__device__ __forceinline__ void march_segments(const BrickParams& P, const T* tile, const SegRec* segs,
+                                               int nseg, int warp, int lane) {
+    constexpr int PER_WARP = 32 / G;
+    const int q = lane / G, r = lane % G;
+    const unsigned int gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (q * G);
+    for (int s0 = warp * PER_WARP; s0 < nseg; s0 += (kBrickThreads / 32) * PER_WARP) {
+        // groups past the end of the list repeat the last record (no atomics)
+        const int si = min(s0 + q, nseg - 1);
+        const SegRec s = segs[si];
+        const int n = s.n & 0x7fffffff;
+        const int iters = (int)__reduce_max_sync(0xffffffffu, (unsigned int)((n + U * G - 1) / (U * G)));
+        float m;
+        if (!__any_sync(0xffffffffu, s.n < 0))
+            m = group_max<T, G, U, false>(tile, s, n, r, iters);
+        else
+            m = group_max<T, G, U, true>(tile, s, n, r, iters);
+        const unsigned int e = __reduce_max_sync(gmask, ord_enc(m));
+        if (r == 0 && s0 + q < nseg) atomicMax(&P.out_enc[s.pix], e);
+    }
+}
+
+// The brick pass.  Two CTAs per SM, each with one staged cell: while a CTA
+// waits for the TMA load of its next cell it already turns that cell's pixel
+// rectangle into segment records, and the other CTA of the SM marches.
+template <typename T>
+__global__ void __launch_bounds__(kBrickThreads, 2)
+k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BrickParams P,
+            const CellDesc* __restrict__ list, const int* __restrict__ count) {
     using G = TileGeom<T>;
     extern __shared__ __align__(128) unsigned char smem[];
-    SegRec* segs = reinterpret_cast<SegRec*>(smem + 2 * G::STRIDE);
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_unit[2];
-    __shared__ int4 s_rect[2], s_coord[2];
-    __shared__ float3 s_lo[2];
-    __shared__ int s_nseg;
+    T* tile = reinterpret_cast<T*>(smem);
+    SegRec* segs = reinterpret_cast<SegRec*>(smem + G::STRIDE);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ CellDesc s_desc[2];
+    __shared__ int s_u[2];
+    __shared__ int s_cnt[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nunits = P.nbricks * P.ncells_x * P.ncells_y * P.ncells_z;
+    const int nvalid = *count;
 
-    // thread 0: claim the next unit with work, record it in slot b and start
-    // its TMA load into buffer b
-    auto advance = [&](int b) {
-        int u;
-        for (;;) {
-            u = atomicAdd(P.work, 1);
-            if (u >= nunits) break;
-            float3 lo;
-            int4 rect, coord;
-            if (unit_geometry<T>(P, u, lo, rect, coord)) {
-                s_rect[b] = rect;
-                s_coord[b] = coord;
-                s_lo[b] = lo;
-                break;
-            }
-        }
-        s_unit[b] = u;
-        if (u < nunits) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bar[b], (uint32_t)G::BYTES);
-            const int4 c = s_coord[b];
-            tma_load_4d(smem + b * G::STRIDE, &tmap, &bar[b], c.x, c.y, c.z, c.w);
-        }
+    auto claim = [&](int slot) {  // thread 0: next unit into descriptor slot
+        const int u = atomicAdd(P.work, 1);
+        s_u[slot] = u;
+        if (u < nvalid) s_desc[slot] = list[u];
+    };
+    auto load = [&](const CellDesc& d) {  // thread 0: stage a cell
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar, (uint32_t)G::BYTES);
+        tma_load_4d(tile, &tmap, &bar, d.coord.x, d.coord.y, d.coord.z, d.coord.w);
     };
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&bar, 1);
         fence_mbar_init();
-        advance(0);
+        s_cnt[0] = 0;
+        s_cnt[1] = 0;
+        claim(0);
+        if (s_u[0] < nvalid) {
+            load(s_desc[0]);
+            claim(1);
+        }
     }
     __syncthreads();
+    if (s_u[0] >= nvalid) return;
 
-    uint32_t phase[2] = {0u, 0u};
-    int buf = 0;
+    int cur = 0, chunk = 0, c0 = 0;
+    uint32_t phase = 0;
+    build_segments<T>(P, s_desc[cur], 0, segs, &s_cnt[0], tid);
+    bool ok = mbar_wait(&bar, phase, P.status);
+    phase ^= 1u;
+    if (!__syncthreads_and(ok)) return;  // no copy is in flight after a failed wait of the only load
     for (;;) {
-        if (s_unit[buf] >= nunits) break;
-        if (tid == 0) advance(buf ^ 1);  // prefetch the next unit into the other buffer
-        const bool ok = mbar_wait(&bar[buf], phase[buf], P.status);
-        phase[buf] ^= 1u;
-        if (!__syncthreads_and(ok)) {
-            // a load did not complete: wait (bounded) for the other buffer's load,
-            // if one was issued, so that no copy lands in released shared memory
-            if (tid == 0 && s_unit[buf ^ 1] < nunits) mbar_wait(&bar[buf ^ 1], phase[buf ^ 1], nullptr);
-            return;
+        const int nseg = s_cnt[chunk & 1];
+        if (tid == 0) s_cnt[(chunk + 1) & 1] = 0;
+        march_segments<T, kGroup, kUnroll>(P, tile, segs, nseg, warp, lane);
+        __syncthreads();
+        ++chunk;
+        const int4 rect = s_desc[cur].rect;
+        const int npx = (rect.z - rect.x + 1) * (rect.w - rect.y + 1);
+        c0 += kSegCap;
+        if (c0 < npx) {  // more pixels of the same cell
+            build_segments<T>(P, s_desc[cur], c0, segs, &s_cnt[chunk & 1], tid);
+            __syncthreads();
+            continue;
         }
-        const T* tile = reinterpret_cast<const T*>(smem + buf * G::STRIDE);
-        const int4 rect = s_rect[buf];
-        const float3 lo = s_lo[buf];
-        const int rw = rect.z - rect.x + 1;
-        const int npx = rw * (rect.w - rect.y + 1);
-        for (int c0 = 0; c0 < npx; c0 += kSegCap) {
-            if (tid == 0) s_nseg = 0;
-            __syncthreads();
-            const int c1 = min(npx, c0 + kSegCap);
-            // phase 1: one thread per pixel of the rectangle -> segment records
-            constexpr int PER = kSegCap / kBrickThreads;
-            int2 kr[PER];
-            int pxv[PER], pyv[PER];
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int i = c0 + tid + q * kBrickThreads;
-                kr[q] = make_int2(0, 0);
-                pyv[q] = rect.y + i / rw;
-                pxv[q] = rect.x + i % rw;
-                if (i < c1) kr[q] = P.krange[pyv[q] * P.cam.width + pxv[q]];
-            }
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                if (kr[q].x >= kr[q].y) continue;
-                SegRec s;
-                if (make_segment<T>(P, pxv[q], pyv[q], kr[q], lo, s)) segs[atomicAdd(&s_nseg, 1)] = s;
-            }
-            __syncthreads();
-            // phase 2: one warp per segment, lanes on consecutive samples
-            const int nseg = s_nseg;
-            for (int si = warp; si < nseg; si += kBrickThreads / 32) {
-                const SegRec s = segs[si];
-                const int n = s.n & 0x7fffffff;
-                float m = s.n >= 0 ? segment_max<T, false>(tile, s.gx, s.gy, s.gz, s.ex, s.ey, s.ez, n, lane)
-                                   : segment_max<T, true>(tile, s.gx, s.gy, s.gz, s.ex, s.ey, s.ez, n, lane);
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-                if (lane == 0) atomicMax(&P.out_enc[s.pix], ord_enc(m));
-            }
-            __syncthreads();
-        }
-        buf ^= 1;
+        const int nxt = cur ^ 1;
+        if (s_u[nxt] >= nvalid) break;
+        if (tid == 0) load(s_desc[nxt]);
+        cur = nxt;
+        c0 = 0;
+        build_segments<T>(P, s_desc[cur], 0, segs, &s_cnt[chunk & 1], tid);
+        if (tid == 0) claim(cur ^ 1);
+        ok = mbar_wait(&bar, phase, P.status);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) return;
     }
 }
 
@@ -425,12 +489,17 @@ __global__ void k_mip_finalize(const __grid_constant__ PixelParams P) {
 }
 
 template <typename T>
-cudaError_t launch_t(const void* tmap, const BrickParams& p, int grid, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_brick_mip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TileGeom<T>::SMEM);
+cudaError_t launch_t(const void* tmap, const BrickParams& p, int grid, void* cells, cudaStream_t s) {
+    CellDesc* list = reinterpret_cast<CellDesc*>(static_cast<char*>(cells) + 256);
+    int* count = static_cast<int*>(cells);
+    const int nunits = p.nbricks * p.ncells_x * p.ncells_y * p.ncells_z;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_brick_mip<T><<<grid, kBrickThreads, TileGeom<T>::SMEM, s>>>(
-        *static_cast<const CUtensorMap*>(tmap), p);
+    k_cell_list<T><<<std::min((nunits + 255) / 256, 4096), 256, 0, s>>>(p, list, count);
+    e = cudaFuncSetAttribute(k_brick_mip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileGeom<T>::SMEM);
+    if (e != cudaSuccess) return e;
+    k_brick_mip<T><<<grid, kBrickThreads, TileGeom<T>::SMEM, s>>>(*static_cast<const CUtensorMap*>(tmap), p,
+                                                                  list, count);
     return cudaGetLastError();
 }
 
@@ -474,11 +543,13 @@ cudaError_t launch_mip_finalize(const PixelParams& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_brick_mip(const void* tmap, const BrickParams& p, vr_dtype dt, int grid,
+size_t brick_cells_bytes(long long nunits) { return 256 + (size_t)nunits * sizeof(CellDesc); }
+
+cudaError_t launch_brick_mip(const void* tmap, const BrickParams& p, vr_dtype dt, int grid, void* cells,
                              cudaStream_t s) {
-    if (dt == VR_F32) return launch_t<float>(tmap, p, grid, s);
-    if (dt == VR_F16) return launch_t<__half>(tmap, p, grid, s);
-    return launch_t<__nv_bfloat16>(tmap, p, grid, s);
+    if (dt == VR_F32) return launch_t<float>(tmap, p, grid, cells, s);
+    if (dt == VR_F16) return launch_t<__half>(tmap, p, grid, cells, s);
+    return launch_t<__nv_bfloat16>(tmap, p, grid, cells, s);
 }
 
 }  // namespace vr

@@ -108,8 +108,11 @@ cudaError_t launch_march(const MarchParams& p, vr_dtype dt, int grid, cudaStream
 int march_blocks_per_sm(vr_dtype dt, int mode);
 cudaError_t launch_pixel_setup(const PixelParams& p, cudaStream_t s);
 cudaError_t launch_mip_finalize(const PixelParams& p, cudaStream_t s);
-cudaError_t launch_brick_mip(const void* tmap, const BrickParams& p, vr_dtype dt, int grid,
+// `cells` is per-context scratch of brick_cells_bytes(units) bytes (a counter and the
+// per-view list of cells with work); the brick kernel's work counter is p.work.
+cudaError_t launch_brick_mip(const void* tmap, const BrickParams& p, vr_dtype dt, int grid, void* cells,
                              cudaStream_t s);
+size_t brick_cells_bytes(long long nunits);
 // Cell (staging unit) edge lengths for a storage type; the brick edge must be a
 // multiple of each.
 void brick_cell_dims(vr_dtype dt, int* cx, int* cy, int* cz);
