@@ -174,6 +174,26 @@ vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams);
  */
 vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, void* stream);
 
+/*
+ * Adjoint (reverse-mode derivative) of vr_render for the current cube, table
+ * and cameras.  dL_dimg (DEVICE, ncams x height x width x 4 float32, the
+ * layout vr_render writes) holds dL/dI of a scalar loss L with respect to the
+ * image of `mode`.  Outputs (DEVICE, overwritten, not accumulated):
+ *   dL_dtf  (n x 4 float32): dL/d(table entry, channel), through the
+ *           node-centred interpolation (zero slope where the lookup clamps);
+ *   dL_dvol (nx*ny*nz float32, x fastest, may be NULL): dL/d(stored voxel
+ *           value), through the trilinear weights (clamped corners included).
+ * Composite: C = sum_k T_k a_k c_k and A = 1 - T_n over the executed samples
+ * (termination is not differentiated); the forward is recomputed segment by
+ * segment from per-segment checkpoints of T and swept back to front.  MIP:
+ * the gradient reaches the first sample that attains the maximum.
+ * Table partials are FP32 per block and summed in FP64.
+ * Errors as vr_render; VR_ERR_UNSUPPORTED (reported by the next call) if a
+ * ray needs more than 320 checkpoint segments (about 10 000 samples).
+ */
+vr_status vr_render_backward(vr_ctx* ctx, vr_mode mode, const float* dL_dimg, float* dL_dtf,
+                             float* dL_dvol, void* stream);
+
 /* Select the kernel family used by later vr_render calls (see vr_path).
  * A path that cannot serve a request makes vr_render return
  * VR_ERR_UNSUPPORTED. */

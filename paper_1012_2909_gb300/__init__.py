@@ -72,6 +72,7 @@ SIGNATURES = {
     "vr_set_camera": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "vr_render": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "vr_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
+    "vr_render_backward": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
     "vr_set_sample_counter": (ctypes.c_int, [_P, _P]),
     "vr_set_kernel_events": (ctypes.c_int, [_P, _P, _P]),
     "vr_render_mip_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -185,6 +186,16 @@ def vr_render(ctx, mode: str, out_rgba, out_max=None, stream=None, device: int =
     _check(ctx, st, "vr_render")
 
 
+def vr_render_backward(ctx, mode: str, dL_dimg, dL_dtf, dL_dvol=None, stream=None, device: int = 0):
+    """dL_dimg (ncams, H, W, 4), dL_dtf (n, 4), dL_dvol (nz, ny, nx) or None: device float32."""
+    lib = load_library()
+    st = lib.vr_render_backward(ctx, MODES[mode], ctypes.c_void_p(dL_dimg.data_ptr()),
+                                ctypes.c_void_p(dL_dtf.data_ptr()),
+                                None if dL_dvol is None else ctypes.c_void_p(dL_dvol.data_ptr()),
+                                _stream_handle(stream, device))
+    _check(ctx, st, "vr_render_backward")
+
+
 VR_NOALLOC_MAX_PIXELS = 1 << 21
 
 
@@ -277,3 +288,75 @@ class Renderer:
             out_max = torch.empty((n, h, w), dtype=torch.float32, device=self.torch_device)
         vr_render(self.ctx, mode, out, out_max, stream, self.device)
         return (out, out_max) if with_max else out
+
+
+# ------------------------------------------------------------------ autograd
+def _autograd_function():
+    import torch
+
+    class VolumeRenderFunction(torch.autograd.Function):
+        """image = render(tf, volume); backward calls vr_render_backward.
+
+        The renderer must hold the cube `volume` (VolumeRenderer.render loads it when the
+        tensor changes) and the table `tf`; both are copied into the library."""
+
+        @staticmethod
+        def forward(ctx, tf, volume, renderer, mode):
+            out = renderer.render(mode)
+            ctx.renderer = renderer
+            ctx.mode = mode
+            ctx.tf_shape = tuple(tf.shape)
+            ctx.vol_shape = tuple(volume.shape) if volume is not None else None
+            ctx.need_vol = volume is not None and volume.requires_grad
+            return out
+
+        @staticmethod
+        def backward(ctx, grad):
+            r = ctx.renderer
+            dtf = torch.empty(ctx.tf_shape, dtype=torch.float32, device=r.torch_device)
+            dvol = (torch.empty(ctx.vol_shape, dtype=torch.float32, device=r.torch_device)
+                    if ctx.need_vol else None)
+            vr_render_backward(r.ctx, ctx.mode, grad.contiguous().float(), dtf, dvol,
+                               device=r.device)
+            return dtf, dvol, None, None
+
+    return VolumeRenderFunction
+
+
+_VRF = None
+
+
+class VolumeRenderer(Renderer):
+    """Renderer whose render(tf, volume) takes part in torch autograd: gradients flow to
+    the transfer-function table and (if it requires grad) the float32 volume."""
+
+    def __init__(self, device=0, brick=128, step=0.5, ert=0.99, vmin=-1.0, vmax=20.0,
+                 storage="f32"):
+        super().__init__(device, brick, step, ert)
+        self.vmin, self.vmax, self.storage = float(vmin), float(vmax), storage
+        self._vol_key = None
+
+    def render(self, mode="composite", out=None, out_max=None, with_max=False, stream=None,
+               tf=None, volume=None):
+        if tf is None:
+            return super().render(mode, out, out_max, with_max, stream)
+        global _VRF
+        if _VRF is None:
+            _VRF = _autograd_function()
+        key = (id(volume), volume._version, volume.data_ptr()) if volume is not None else None
+        if volume is not None and key != self._vol_key:
+            self.load_cube(volume.detach().contiguous(), self.storage, stream)
+            self._vol_key = key
+        self.set_transfer_function(tf.detach().float().cpu().numpy(), self.vmin, self.vmax)
+        return _VRF.apply(tf, volume, _Plain(self), mode)
+
+
+class _Plain:
+    """The non-autograd face of a VolumeRenderer (what the autograd function calls)."""
+
+    def __init__(self, r):
+        self._r = r
+        self.ctx, self.device, self.torch_device = r.ctx, r.device, r.torch_device
+
+    def render(self, mode):
+        return Renderer.render(self._r, mode)

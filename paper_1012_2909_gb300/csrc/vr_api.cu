@@ -49,6 +49,8 @@ struct vr_ctx {
     int2* krange = nullptr;        // per-pixel sample range of the brick pass
     unsigned int* enc = nullptr;   // per-pixel running maximum when out_max is NULL
     long long scratch_pix = 0;
+    float* tf_partials = nullptr;  // adjoint: per-block table-gradient partials
+    size_t tf_partials_n = 0;
     int* status_host = nullptr;    // mapped, page-locked device status word
     int* status_dev = nullptr;
     unsigned long long* sample_counter = nullptr;  // caller-owned
@@ -278,6 +280,7 @@ vr_status vr_destroy(vr_ctx* ctx) {
         if (ctx->work) cudaFree(ctx->work);
         if (ctx->krange) cudaFree(ctx->krange);
         if (ctx->enc) cudaFree(ctx->enc);
+        if (ctx->tf_partials) cudaFree(ctx->tf_partials);
         if (ctx->status_host) cudaFreeHost(ctx->status_host);
     }
     delete ctx;
@@ -684,6 +687,73 @@ vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, 
         return render_brick_mip(ctx, out_rgba, out_max, s);
     }
     return render_ray(ctx, mode, out_rgba, out_max, s);
+}
+
+vr_status vr_render_backward(vr_ctx* ctx, vr_mode mode, const float* dL_dimg, float* dL_dtf, float* dL_dvol,
+                             void* stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (mode != VR_COMPOSITE && mode != VR_MIP)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_render_backward: bad mode");
+    if (!dL_dimg || !dL_dtf)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_render_backward: dL_dimg and dL_dtf are required");
+    if (reinterpret_cast<uintptr_t>(dL_dimg) % 16 || reinterpret_cast<uintptr_t>(dL_dtf) % 4 ||
+        reinterpret_cast<uintptr_t>(dL_dvol) % 4)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_render_backward: dL_dimg must be 16-byte aligned");
+    if (!ctx->has_cube) return fail(ctx, VR_ERR_STATE, "vr_render_backward: no cube loaded");
+    if (!ctx->has_tf) return fail(ctx, VR_ERR_STATE, "vr_render_backward: no transfer function set");
+    if (ctx->cams.empty()) return fail(ctx, VR_ERR_STATE, "vr_render_backward: no camera set");
+    if (*ctx->status_host != 0) {
+        const int code = *ctx->status_host;
+        *ctx->status_host = 0;
+        return fail(ctx, code == 2 ? VR_ERR_UNSUPPORTED : VR_ERR_INTERNAL,
+                    code == 2 ? "an earlier backward pass met a ray with more checkpoint segments than it keeps"
+                              : "an earlier device pass stopped on a bounded wait");
+    }
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VR_CK(cudaGetLastError(), "vr_render_backward: pending CUDA error");
+    const int ncams = (int)ctx->cams.size();
+    const int nbatch = (ncams + kMaxLaunchCams - 1) / kMaxLaunchCams;
+    const int ntf = (int)ctx->tf.size();
+    const int grid = ctx->num_sms * adjoint_blocks_per_sm(ctx->dtype, mode, ntf);
+    const size_t need = (size_t)nbatch * grid * ntf * 4;
+    if (need > ctx->tf_partials_n) {
+        if (ctx->tf_partials) cudaFree(ctx->tf_partials);
+        ctx->tf_partials = nullptr;
+        ctx->tf_partials_n = 0;
+        VR_CK(cudaMalloc(&ctx->tf_partials, need * sizeof(float)), "vr_render_backward: partials");
+        ctx->tf_partials_n = need;
+    }
+    if (dL_dvol)
+        VR_CK(cudaMemsetAsync(dL_dvol, 0, sizeof(float) * (size_t)ctx->nx * ctx->ny * ctx->nz, s),
+              "vr_render_backward: clear dL_dvol");
+    VR_CK(cudaMemsetAsync(ctx->work, 0, sizeof(int) * nbatch, s), "vr_render_backward: scheduler reset");
+    AdjParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.vol = vol_dev(ctx);
+    P.tf = tf_dev(ctx);
+    P.width = ctx->cams[0].width;
+    P.height = ctx->cams[0].height;
+    P.mode = mode;
+    P.tiles_x = (P.width + kTileW - 1) / kTileW;
+    P.tiles_y = (P.height + kTileH - 1) / kTileH;
+    P.step = ctx->opt.step;
+    P.ert = (float)ctx->opt.ert;
+    P.dvol = dL_dvol;
+    P.status = ctx->status_dev;
+    const long long img = (long long)P.width * P.height;
+    for (int b = 0; b < nbatch; ++b) {
+        const int c0 = b * kMaxLaunchCams;
+        P.ncams = std::min(kMaxLaunchCams, ncams - c0);
+        for (int i = 0; i < P.ncams; ++i) P.cams[i] = ctx->cams[(size_t)(c0 + i)];
+        P.dimg = reinterpret_cast<const float4*>(dL_dimg) + (long long)c0 * img;
+        P.tf_partials = ctx->tf_partials + (size_t)b * grid * ntf * 4;
+        P.work = ctx->work + b;
+        VR_CK(launch_adjoint(P, ctx->dtype, grid, s), "vr_render_backward: adjoint launch");
+    }
+    VR_CK(launch_tfgrad_reduce(ctx->tf_partials, nbatch * grid, ntf * 4, dL_dtf, s),
+          "vr_render_backward: table reduction");
+    return VR_OK;
 }
 
 const char* vr_last_error(const vr_ctx* ctx) {

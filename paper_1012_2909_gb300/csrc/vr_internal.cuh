@@ -87,6 +87,24 @@ struct BrickParams {
     int* status;             // device status word (0 = ok)
 };
 
+// Launch parameters of the adjoint (one batch of at most kMaxLaunchCams cameras).
+struct AdjParams {
+    VolDev vol;
+    TFDev tf;
+    CamDev cams[kMaxLaunchCams];
+    int ncams, width, height, mode;
+    int tiles_x, tiles_y;
+    int pad0, pad1;
+    double step;
+    float ert;
+    int pad2;
+    const float4* dimg;   // dL/dI of camera 0 of this launch
+    float* dvol;          // dL/dvoxel, linear x-fastest (may be null)
+    float* tf_partials;   // per-block table partials of this launch (grid x ntf x 4)
+    int* work;            // zeroed work counter of this launch
+    int* status;          // device status word
+};
+
 // Per-pixel set-up and finalisation around the brick pass.
 struct PixelParams {
     VolDev vol;
@@ -119,6 +137,10 @@ void brick_cell_dims(vr_dtype dt, int* cx, int* cy, int* cz);
 // TMA box of one cell (cell + 2 ghost, x padded to 16 bytes), in elements.
 void brick_box_dims(vr_dtype dt, int* bx, int* by, int* bz);
 constexpr int kMarchThreads = 128;
+int adjoint_threads();
+int adjoint_blocks_per_sm(vr_dtype dt, int mode, int ntf);
+cudaError_t launch_adjoint(const AdjParams& p, vr_dtype dt, int grid, cudaStream_t s);
+cudaError_t launch_tfgrad_reduce(const float* partials, int nblocks, int nval, float* out, cudaStream_t s);
 // Brick-path MIP pieces used by the allocation-free entry point (vr_api.cu).
 vr_status brick_mip_precheck(vr_ctx* ctx, float* out_rgba, float* out_max, int* device,
                              long long* pixels);
