@@ -520,12 +520,15 @@ vr_status ensure_pixel_scratch(vr_ctx* ctx, long long npix) {
     return VR_OK;
 }
 
-// MIP through the brick pass: per camera, pixel set-up (sample ranges, running
-// maxima), the staged brick pass, and the transfer-function finalisation.
+// MIP through the brick pass, up to kMaxLaunchCams cameras per pass over the
+// cube: pixel set-up per camera (sample ranges, running maxima), one staged
+// brick pass for the batch, transfer-function finalisation per camera.
 vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStream_t s) {
     const int W = ctx->cams[0].width, H = ctx->cams[0].height;
     const long long img = (long long)W * H;
-    vr_status st = ensure_pixel_scratch(ctx, img);
+    const int ncams = (int)ctx->cams.size();
+    const int per = std::min(ncams, kMaxLaunchCams);
+    vr_status st = ensure_pixel_scratch(ctx, img * per);
     if (st != VR_OK) return st;
     PixelParams pp;
     std::memset(&pp, 0, sizeof(pp));
@@ -534,11 +537,12 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
     pp.step = ctx->opt.step;
     pp.width = W;
     pp.height = H;
-    pp.krange = ctx->krange;
     BrickParams bp;
     std::memset(&bp, 0, sizeof(bp));
     bp.vol = pp.vol;
     bp.step = (float)ctx->opt.step;
+    bp.width = W;
+    bp.height = H;
     int cx, cy, cz;
     brick_cell_dims(ctx->dtype, &cx, &cy, &cz);
     bp.ncells_x = ctx->B / cx;
@@ -547,24 +551,32 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
     bp.nbricks = ctx->nbx * ctx->nby * ctx->nbz;
     bp.krange = ctx->krange;
     bp.status = ctx->status_dev;
-    const int ncams = (int)ctx->cams.size();
     const int grid = 2 * ctx->num_sms;
-    for (int i = 0; i < ncams; ++i) {
-        const CamDev& cd = ctx->cams[(size_t)i];
-        if (!cam_ff(cd, bp.cam))
-            return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: camera basis is singular");
-        pp.cam = cd;
-        pp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)i * img;
-        pp.out_max = out_max ? out_max + (long long)i * img : nullptr;
-        pp.enc = out_max ? reinterpret_cast<unsigned int*>(pp.out_max) : ctx->enc;
-        bp.out_enc = pp.enc;
-        bp.work = ctx->work + kMaxLaunchCams + (i % 4096);
+    for (int c0 = 0; c0 < ncams; c0 += per) {
+        const int nb = std::min(per, ncams - c0);
+        bp.ncams = nb;
+        unsigned int* enc = out_max ? reinterpret_cast<unsigned int*>(out_max + (long long)c0 * img) : ctx->enc;
+        for (int i = 0; i < nb; ++i) {
+            if (!cam_ff(ctx->cams[(size_t)(c0 + i)], bp.cams[i]))
+                return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: camera basis is singular");
+            pp.cam = ctx->cams[(size_t)(c0 + i)];
+            pp.krange = ctx->krange + (long long)i * img;
+            pp.enc = enc + (long long)i * img;
+            VR_CK(launch_pixel_setup(pp, s), "vr_render: pixel set-up");
+        }
+        bp.out_enc = enc;
+        bp.work = ctx->work + kMaxLaunchCams + (c0 / per) % 4096;
         VR_CK(cudaMemsetAsync(bp.work, 0, sizeof(int), s), "vr_render: scheduler reset");
-        VR_CK(launch_pixel_setup(pp, s), "vr_render: pixel set-up");
-        if (i == 0 && ctx->ev_start) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
+        if (c0 == 0 && ctx->ev_start) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
         VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, grid, ctx->cells, s), "vr_render: brick pass");
-        if (i == ncams - 1 && ctx->ev_stop) VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
-        VR_CK(launch_mip_finalize(pp, s), "vr_render: finalise");
+        if (c0 + nb >= ncams && ctx->ev_stop) VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
+        for (int i = 0; i < nb; ++i) {
+            pp.cam = ctx->cams[(size_t)(c0 + i)];
+            pp.enc = enc + (long long)i * img;
+            pp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)(c0 + i) * img;
+            pp.out_max = out_max ? out_max + (long long)(c0 + i) * img : nullptr;
+            VR_CK(launch_mip_finalize(pp, s), "vr_render: finalise");
+        }
     }
     return VR_OK;
 }
@@ -629,9 +641,12 @@ vr_status brick_mip_with_scratch(vr_ctx* ctx, float* out_rgba, float* out_max, c
     bp.krange = krange;
     bp.status = ctx->status_dev;
     bp.work = work;
+    bp.width = W;
+    bp.height = H;
+    bp.ncams = 1;
     const int ncams = (int)ctx->cams.size();
     for (int i = 0; i < ncams; ++i) {
-        if (!cam_ff(ctx->cams[(size_t)i], bp.cam))
+        if (!cam_ff(ctx->cams[(size_t)i], bp.cams[0]))
             return fail(ctx, VR_ERR_INVALID_ARG, "camera basis is singular");
         pp.cam = ctx->cams[(size_t)i];
         pp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)i * img;

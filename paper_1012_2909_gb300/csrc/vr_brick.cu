@@ -147,10 +147,10 @@ __device__ bool cell_rect(const CamFF& c, float3 lo, float3 hi, int4& r) {
     return px0 <= px1 && py0 <= py1;
 }
 
-// Geometry of work unit u = brick * ncells + cell: lower corner, pixel
-// rectangle and TMA coordinates; false if the unit has no work.
+// Geometry of work unit u = brick * ncells + cell: lower corner and TMA
+// coordinates; false if the cell lies outside the cube or its brick is absent.
 template <typename T>
-__device__ bool unit_geometry(const BrickParams& P, int u, float3& lo, int4& rect, int4& coord) {
+__device__ bool unit_cell(const BrickParams& P, int u, float3& lo, int4& coord) {
     using C = Cell<T>;
     const VolDev& v = P.vol;
     const int ncells = P.ncells_x * P.ncells_y * P.ncells_z;
@@ -161,19 +161,23 @@ __device__ bool unit_geometry(const BrickParams& P, int u, float3& lo, int4& rec
     const int ox = bx * v.B + cx * C::CX, oy = by * v.B + cy * C::CY, oz = bz * v.B + cz * C::CZ;
     if (ox >= v.nx || oy >= v.ny || oz >= v.nz) return false;
     lo = make_float3((float)ox, (float)oy, (float)oz);
-    const float3 hi = make_float3((float)(ox + C::CX), (float)(oy + C::CY), (float)(oz + C::CZ));
-    if (!cell_rect(P.cam, lo, hi, rect)) return false;
     coord = make_int4(cx * C::CX, cy * C::CY, cz * C::CZ, v.table[brick]);
     return coord.w >= 0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool cam_cell_rect(const CamFF& c, float3 lo, int4& rect) {
+    using C = Cell<T>;
+    const float3 hi = make_float3(lo.x + (float)C::CX, lo.y + (float)C::CY, lo.z + (float)C::CZ);
+    return cell_rect(c, lo, hi, rect);
 }
 
 // Segment of pixel (px, py) inside the cell whose lower corner is lo; false if
 // the ray owns no sample there.
 template <typename T>
-__device__ __forceinline__ bool make_segment(const BrickParams& P, int px, int py, int2 kr,
-                                             float3 lo, SegRec& s) {
+__device__ __forceinline__ bool make_segment(const BrickParams& P, const CamFF& c, int px, int py,
+                                             int2 kr, float3 lo, SegRec& s) {
     using C = Cell<T>;
-    const CamFF& c = P.cam;
     const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
     float o[3], e[3];
     {
@@ -268,7 +272,7 @@ __device__ __forceinline__ bool make_segment(const BrickParams& P, int px, int p
         const float top = (float)ext[a] + 1.0f - 1e-3f;
         inside = inside && g[a] >= 1e-3f && g[a] < top && gend >= 1e-3f && gend < top;
     }
-    s.pix = py * c.width + px;
+    s.pix = py * c.width + px;  // the caller adds the camera's image offset
     s.n = (kb - ka) | (inside ? 0 : (int)0x80000000u);
     s.gx = g[0];
     s.gy = g[1];
@@ -281,11 +285,11 @@ __device__ __forceinline__ bool make_segment(const BrickParams& P, int px, int p
 
 struct CellDesc {
     float4 lo;    // lower corner (world voxels)
-    int4 rect;    // pixel rectangle px0, py0, px1, py1 (inclusive)
     int4 coord;   // TMA coordinates x, y, z (slot elements), slot
+    int4 rect0;   // pixel rectangle of camera 0 (empty: x > z)
 };
 
-// Compacted list of the cells that some pixel of this view can reach, in
+// Compacted list of the cells that some pixel of some camera can reach, in
 // roughly linear cell order (warp-aggregated appends), so that neighbouring
 // cells -- which share ghost voxels through L2 -- run close in time.
 template <typename T>
@@ -296,8 +300,18 @@ __global__ void k_cell_list(const __grid_constant__ BrickParams P, CellDesc* __r
     for (int u0 = blockIdx.x * blockDim.x; u0 < nunits; u0 += gridDim.x * blockDim.x) {
         const int u = u0 + threadIdx.x;
         float3 lo;
-        int4 rect, coord;
-        const bool ok = u < nunits && unit_geometry<T>(P, u, lo, rect, coord);
+        int4 coord;
+        bool ok = u < nunits && unit_cell<T>(P, u, lo, coord);
+        int4 rect0 = make_int4(0, 0, -1, -1);
+        if (ok) {
+            bool any = cam_cell_rect<T>(P.cams[0], lo, rect0);
+            if (!any) rect0 = make_int4(0, 0, -1, -1);
+            for (int c = 1; c < P.ncams && !any; ++c) {
+                int4 rect;
+                any = cam_cell_rect<T>(P.cams[c], lo, rect);
+            }
+            ok = any;
+        }
         const unsigned int m = __ballot_sync(0xffffffffu, ok);
         int base = 0;
         if (lane == 0 && m) base = atomicAdd(count, __popc(m));
@@ -305,22 +319,24 @@ __global__ void k_cell_list(const __grid_constant__ BrickParams P, CellDesc* __r
         if (ok) {
             CellDesc d;
             d.lo = make_float4(lo.x, lo.y, lo.z, 0.f);
-            d.rect = rect;
             d.coord = coord;
+            d.rect0 = rect0;
             list[base + __popc(m & ((1u << lane) - 1u))] = d;
         }
     }
 }
 
-// One chunk of a cell's pixel rectangle -> segment records (phase 1).
-template <typename T>
-__device__ __forceinline__ void build_segments(const BrickParams& P, const CellDesc& d, int c0,
-                                               SegRec* segs, int* cnt, int tid) {
-    const int4 rect = d.rect;
+// One chunk of camera cam's pixel rectangle of a cell -> segment records (phase 1).
+template <typename T, bool ONE>
+__device__ __forceinline__ void build_segments(const BrickParams& P, int cam_, int4 rect, float3 lo,
+                                               int c0, SegRec* segs, int* cnt, int tid) {
+    const int cam = ONE ? 0 : cam_;  // one camera: constant-offset parameter reads
+    const CamFF& c = P.cams[cam];
+    const long long img = (long long)P.width * P.height;
+    const int2* kr_img = P.krange + (long long)cam * img;
     const int rw = rect.z - rect.x + 1;
     const int npx = rw * (rect.w - rect.y + 1);
     const int c1 = min(npx, c0 + kSegCap);
-    const float3 lo = make_float3(d.lo.x, d.lo.y, d.lo.z);
     constexpr int PER = kSegCap / kBrickThreads;
     int2 kr[PER];
     int pxv[PER], pyv[PER];
@@ -330,13 +346,16 @@ __device__ __forceinline__ void build_segments(const BrickParams& P, const CellD
         kr[q] = make_int2(0, 0);
         pyv[q] = rect.y + i / rw;
         pxv[q] = rect.x + i % rw;
-        if (i < c1) kr[q] = P.krange[pyv[q] * P.cam.width + pxv[q]];
+        if (i < c1) kr[q] = kr_img[pyv[q] * P.width + pxv[q]];
     }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
         if (kr[q].x >= kr[q].y) continue;
         SegRec s;
-        if (make_segment<T>(P, pxv[q], pyv[q], kr[q], lo, s)) segs[atomicAdd(cnt, 1)] = s;
+        if (make_segment<T>(P, c, pxv[q], pyv[q], kr[q], lo, s)) {
+            s.pix += (int)(cam * img);
+            segs[atomicAdd(cnt, 1)] = s;
+        }
     }
 }
 
@@ -389,8 +408,10 @@ __device__ __forceinline__ void march_segments(const BrickParams& P, const T* ti
 
 // The brick pass.  Two CTAs per SM, each with one staged cell: while a CTA
 // waits for the TMA load of its next cell it already turns that cell's pixel
-// rectangle into segment records, and the other CTA of the SM marches.
-template <typename T>
+// rectangles into segment records, and the other CTA of the SM marches.  A
+// staged cell serves every camera of the launch (the 25 panels of a wall are
+// rendered from one pass over the cube).
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(kBrickThreads, 2)
 k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BrickParams P,
             const CellDesc* __restrict__ list, const int* __restrict__ count) {
@@ -399,41 +420,77 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     T* tile = reinterpret_cast<T*>(smem);
     SegRec* segs = reinterpret_cast<SegRec*>(smem + G::STRIDE);
     __shared__ __align__(8) uint64_t bar;
-    __shared__ CellDesc s_desc[2];
-    __shared__ int s_u[2];
+    // three descriptor slots: the unit in progress, the one being loaded, and the
+    // one being claimed -- a slot is refilled two units after its last reader
+    __shared__ CellDesc s_desc[3];
+    __shared__ int4 s_rect[3][kMaxLaunchCams];
+    __shared__ int s_u[3];
     __shared__ int s_cnt[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nvalid = *count;
-
-    auto claim = [&](int slot) {  // thread 0: next unit into descriptor slot
-        const int u = atomicAdd(P.work, 1);
-        s_u[slot] = u;
-        if (u < nvalid) s_desc[slot] = list[u];
+    const int ncams = ONE ? 1 : P.ncams;
+    // warp 0: claim the next unit into descriptor slot `slot`, with its pixel
+    // rectangle for every camera (camera 0 from the list, the others one lane each)
+    auto claim = [&](int slot) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(P.work, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (lane == 0) s_u[slot] = u;
+        if (u < nvalid) {
+            const CellDesc d = list[u];
+            if (lane == 0) {
+                s_desc[slot] = d;
+                s_rect[slot][0] = d.rect0;
+            }
+            if (lane > 0 && lane < ncams) {
+                int4 r;
+                if (!cam_cell_rect<T>(P.cams[lane], make_float3(d.lo.x, d.lo.y, d.lo.z), r))
+                    r = make_int4(0, 0, -1, -1);
+                s_rect[slot][lane] = r;
+            }
+        }
     };
     auto load = [&](const CellDesc& d) {  // thread 0: stage a cell
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&bar, (uint32_t)G::BYTES);
         tma_load_4d(tile, &tmap, &bar, d.coord.x, d.coord.y, d.coord.z, d.coord.w);
     };
+    // next (camera, first pixel) of the current unit after (cam, c0), or cam = ncams
+    auto next_chunk = [&](int slot, int& cam, int& c0) {
+        for (;;) {
+            if (cam < ncams) {
+                const int4 r = s_rect[slot][cam];
+                const int npx = (r.z - r.x + 1) * (r.w - r.y + 1);
+                if (r.z >= r.x && r.w >= r.y && c0 < npx) return;
+            }
+            if (cam >= ncams) return;
+            ++cam;
+            c0 = 0;
+        }
+    };
 
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-        s_cnt[0] = 0;
-        s_cnt[1] = 0;
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_init(&bar, 1);
+            fence_mbar_init();
+            s_cnt[0] = 0;
+            s_cnt[1] = 0;
+        }
         claim(0);
         if (s_u[0] < nvalid) {
-            load(s_desc[0]);
+            if (lane == 0) load(s_desc[0]);
             claim(1);
         }
     }
     __syncthreads();
     if (s_u[0] >= nvalid) return;
 
-    int cur = 0, chunk = 0, c0 = 0;
+    int cur = 0, chunk = 0, cam = 0, c0 = 0;
     uint32_t phase = 0;
-    build_segments<T>(P, s_desc[cur], 0, segs, &s_cnt[0], tid);
+    next_chunk(cur, cam, c0);
+    float3 lo = make_float3(s_desc[cur].lo.x, s_desc[cur].lo.y, s_desc[cur].lo.z);
+    if (cam < ncams) build_segments<T, ONE>(P, cam, s_rect[cur][cam], lo, c0, segs, &s_cnt[0], tid);
     bool ok = mbar_wait(&bar, phase, P.status);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) return;  // no copy is in flight after a failed wait of the only load
@@ -443,21 +500,24 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
         march_segments<T, kGroup, kUnroll>(P, tile, segs, nseg, warp, lane);
         __syncthreads();
         ++chunk;
-        const int4 rect = s_desc[cur].rect;
-        const int npx = (rect.z - rect.x + 1) * (rect.w - rect.y + 1);
         c0 += kSegCap;
-        if (c0 < npx) {  // more pixels of the same cell
-            build_segments<T>(P, s_desc[cur], c0, segs, &s_cnt[chunk & 1], tid);
+        next_chunk(cur, cam, c0);
+        if (cam < ncams) {  // more pixels of the same cell
+            build_segments<T, ONE>(P, cam, s_rect[cur][cam], lo, c0, segs, &s_cnt[chunk & 1], tid);
             __syncthreads();
             continue;
         }
-        const int nxt = cur ^ 1;
+        const int nxt = cur == 2 ? 0 : cur + 1;
         if (s_u[nxt] >= nvalid) break;
         if (tid == 0) load(s_desc[nxt]);
         cur = nxt;
+        cam = 0;
         c0 = 0;
-        build_segments<T>(P, s_desc[cur], 0, segs, &s_cnt[chunk & 1], tid);
-        if (tid == 0) claim(cur ^ 1);
+        next_chunk(cur, cam, c0);
+        lo = make_float3(s_desc[cur].lo.x, s_desc[cur].lo.y, s_desc[cur].lo.z);
+        if (cam < ncams) build_segments<T, ONE>(P, cam, s_rect[cur][cam], lo, c0, segs, &s_cnt[chunk & 1], tid);
+        // the slot after `cur` was last read two units ago: refill it now
+        if (warp == 0) claim(cur == 2 ? 0 : cur + 1);
         ok = mbar_wait(&bar, phase, P.status);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) return;
@@ -488,6 +548,17 @@ __global__ void k_mip_finalize(const __grid_constant__ PixelParams P) {
     }
 }
 
+template <typename T, bool ONE>
+cudaError_t launch_brick(const void* tmap, const BrickParams& p, int grid, const CellDesc* list, const int* count,
+                         cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_brick_mip<T, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TileGeom<T>::SMEM);
+    if (e != cudaSuccess) return e;
+    k_brick_mip<T, ONE><<<grid, kBrickThreads, TileGeom<T>::SMEM, s>>>(*static_cast<const CUtensorMap*>(tmap), p,
+                                                                       list, count);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_t(const void* tmap, const BrickParams& p, int grid, void* cells, cudaStream_t s) {
     CellDesc* list = reinterpret_cast<CellDesc*>(static_cast<char*>(cells) + 256);
@@ -496,11 +567,8 @@ cudaError_t launch_t(const void* tmap, const BrickParams& p, int grid, void* cel
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     k_cell_list<T><<<std::min((nunits + 255) / 256, 4096), 256, 0, s>>>(p, list, count);
-    e = cudaFuncSetAttribute(k_brick_mip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, TileGeom<T>::SMEM);
-    if (e != cudaSuccess) return e;
-    k_brick_mip<T><<<grid, kBrickThreads, TileGeom<T>::SMEM, s>>>(*static_cast<const CUtensorMap*>(tmap), p,
-                                                                  list, count);
-    return cudaGetLastError();
+    return p.ncams == 1 ? launch_brick<T, true>(tmap, p, grid, list, count, s)
+                        : launch_brick<T, false>(tmap, p, grid, list, count, s);
 }
 
 }  // namespace

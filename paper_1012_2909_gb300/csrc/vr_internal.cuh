@@ -74,10 +74,12 @@ struct CamFF {
     int type, width, height, pad;
 };
 
-// Launch parameters of the brick (object-order) pass for one camera.
+// Launch parameters of the brick (object-order) pass for up to kMaxLaunchCams
+// cameras of one size; per-pixel arrays are camera-major (cam * W * H + pixel).
 struct BrickParams {
     VolDev vol;
-    CamFF cam;
+    CamFF cams[kMaxLaunchCams];
+    int ncams, width, height;
     float step;
     int ncells_x, ncells_y, ncells_z;  // cells per brick along each axis
     int nbricks;

@@ -261,3 +261,26 @@ def test_survey_workload_sampled_pixels(vr, storage):
                          gpu_max=mxs[i][pix] if mode == "mip" else None, max_tol=2e-3)
             print(storage, mode, path, i, st)
     r.close()
+
+
+@pytest.mark.parametrize("storage", ["f16"])
+def test_wall_25_frusta_one_launch(vr, storage):
+    """5 x 5 wall: 25 off-axis frusta of one camera rendered together (one persistent
+    launch per mode); each panel equals the oracle, and the mosaic equals the oracle's
+    render of the single big camera (the panels are exact sub-windows)."""
+    dims = (160, 144, 96)
+    vol = synth.generate(synth.cube_params(*dims, seed=71, nsrc=30, ripple=True, ripple_period=48.0))
+    tf = synth.viridis_ramp_tf()
+    big = synth.orbit_view(dims, 35.0, 5 * 24, 5 * 14)
+    panels = synth.wall_views(big, 5, 5)
+    sc = oracle.Scene(oracle.round_storage(vol, storage), tf, -1.0, 20.0, 0.5, 0.99)
+    for mode in ("composite", "mip"):
+        img, mx = _render(vr, vol, tf, panels, mode, storage=storage, brick=32)
+        mosaic = np.zeros((5 * 14, 5 * 24, 4), np.float32)
+        for i in range(25):
+            rr, cc = divmod(i, 5)
+            mosaic[14 * rr:14 * rr + 14, 24 * cc:24 * cc + 24] = img[i]
+        compare(mosaic.reshape(-1, 4), sc, big, mode, tol=1e-4)
+        for i in (0, 7, 24):
+            compare(img[i].reshape(-1, 4), sc, panels[i], mode, tol=1e-4,
+                    gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
