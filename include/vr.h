@@ -194,6 +194,40 @@ vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, 
 vr_status vr_render_backward(vr_ctx* ctx, vr_mode mode, const float* dL_dimg, float* dL_dtf,
                              float* dL_dvol, void* stream);
 
+/* Launch shape of the kernels (chosen by vr_autotune or set directly).
+ *   tile_w x tile_h: pixels of one warp work item of the image-order path
+ *                    (tile_w * tile_h = 32: one ray per lane);
+ *   block:           threads per CTA of the image-order path (64, 128, 256);
+ *   group:           lanes per ray segment in the brick path (4, 8, 16), i.e.
+ *                    32 / group rays per warp.
+ * Defaults 8 x 4, 128, 8.  Results do not depend on the tuning. */
+typedef struct {
+    int32_t tile_w, tile_h;
+    int32_t block;
+    int32_t group;
+} vr_tuning;
+
+vr_status vr_get_tuning(const vr_ctx* ctx, vr_tuning* out);
+vr_status vr_set_tuning(vr_ctx* ctx, const vr_tuning* tuning);
+
+/* Autotuner: renders `mode` for the current cube and cameras with every
+ * candidate launch shape of the path that serves it (5 tile shapes x 3 block
+ * sizes for the image-order path, 3 group sizes for the brick path), reps
+ * timed renders each after one warm-up (CUDA events on `stream`), keeps the
+ * fastest in the context and returns it (best, best_ms may be NULL).
+ * scratch_rgba: DEVICE output of ncams x height x width x 4 float32.  Blocks
+ * until the timings are in. */
+vr_status vr_autotune(vr_ctx* ctx, vr_mode mode, float* scratch_rgba, int reps, vr_tuning* best,
+                      double* best_ms, void* stream);
+
+/* Graph mode (enable != 0): each vr_render records its launches into a CUDA
+ * graph on a private stream, updates the context's cached executable graph
+ * with it (new cameras, table and output pointers reach the graph this way)
+ * and launches that graph on the caller's stream: one launch per render
+ * however many kernels it takes (the 25 panels of a wall, for instance).
+ * Profiling events (vr_set_kernel_events) are not recorded in graph mode. */
+vr_status vr_set_graph(vr_ctx* ctx, int enable);
+
 /* Select the kernel family used by later vr_render calls (see vr_path).
  * A path that cannot serve a request makes vr_render return
  * VR_ERR_UNSUPPORTED. */

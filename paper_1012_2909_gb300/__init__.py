@@ -51,6 +51,11 @@ class vr_options(ctypes.Structure):
                 ("ert", ctypes.c_double)]
 
 
+class vr_tuning(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("group", ctypes.c_int32)]
+
+
 class vr_cube_info(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
                 ("nbx", ctypes.c_int32), ("nby", ctypes.c_int32), ("nbz", ctypes.c_int32),
@@ -72,6 +77,10 @@ SIGNATURES = {
     "vr_set_camera": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "vr_render": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "vr_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
+    "vr_get_tuning": (ctypes.c_int, [_P, _P]),
+    "vr_set_tuning": (ctypes.c_int, [_P, _P]),
+    "vr_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P]),
+    "vr_set_graph": (ctypes.c_int, [_P, ctypes.c_int]),
     "vr_render_backward": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
     "vr_set_sample_counter": (ctypes.c_int, [_P, _P]),
     "vr_set_kernel_events": (ctypes.c_int, [_P, _P, _P]),
@@ -207,6 +216,34 @@ def vr_render_mip_noalloc(ctx, out_rgba, out_max=None, stream=None, device: int 
                                    None if out_max is None else ctypes.c_void_p(out_max.data_ptr()),
                                    _stream_handle(stream, device))
     _check(ctx, st, "vr_render_mip_noalloc")
+
+
+def vr_get_tuning(ctx) -> dict:
+    t = vr_tuning()
+    _check(ctx, load_library().vr_get_tuning(ctx, ctypes.byref(t)), "vr_get_tuning")
+    return {k: getattr(t, k) for k, _ in vr_tuning._fields_}
+
+
+def vr_set_tuning(ctx, tuning: dict):
+    t = vr_tuning(**{k: int(tuning[k]) for k, _ in vr_tuning._fields_})
+    _check(ctx, load_library().vr_set_tuning(ctx, ctypes.byref(t)), "vr_set_tuning")
+
+
+def vr_autotune(ctx, mode: str, scratch_rgba, reps: int = 5, stream=None, device: int = 0):
+    """Time every candidate launch shape for `mode`; keeps and returns the fastest
+    (dict with the tuning and its ms per render)."""
+    t = vr_tuning()
+    ms = ctypes.c_double()
+    st = load_library().vr_autotune(ctx, MODES[mode], ctypes.c_void_p(scratch_rgba.data_ptr()), int(reps),
+                                    ctypes.byref(t), ctypes.byref(ms), _stream_handle(stream, device))
+    _check(ctx, st, "vr_autotune")
+    d = {k: getattr(t, k) for k, _ in vr_tuning._fields_}
+    d["ms"] = ms.value
+    return d
+
+
+def vr_set_graph(ctx, enable: bool = True):
+    _check(ctx, load_library().vr_set_graph(ctx, int(bool(enable))), "vr_set_graph")
 
 
 def vr_set_path(ctx, path: str = "auto"):
@@ -360,3 +397,33 @@ class _Plain:
 
     def render(self, mode):
         return Renderer.render(self._r, mode)
+
+
+# ------------------------------------------------------------------ autotuning cache
+def autotune(renderer: Renderer, mode: str, reps: int = 5, cache: str | None = None) -> dict:
+    """Pick the launch shape for `mode` on the renderer's current cube and cameras with
+    vr_autotune, remembering the result in a JSON file keyed by GPU, cube, storage type,
+    image size, camera count and mode (so a later run on the same workload reuses it)."""
+    import json
+
+    import torch
+    info = renderer.cube_info()
+    n, h, w = len(renderer.cams), renderer.cams[0]["height"], renderer.cams[0]["width"]
+    key = "|".join(str(x) for x in (torch.cuda.get_device_name(renderer.device), info["nx"], info["ny"],
+                                    info["nz"], info["dtype"], info["brick"], w, h, n, mode))
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+    if key in table:
+        vr_set_tuning(renderer.ctx, table[key])
+        return dict(table[key], cached=True)
+    scratch = torch.empty((n, h, w, 4), dtype=torch.float32, device=renderer.torch_device)
+    best = vr_autotune(renderer.ctx, mode, scratch, reps, device=renderer.device)
+    if cache:
+        table[key] = best
+        tmp = cache + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1)
+        os.replace(tmp, cache)
+    return dict(best, cached=False)

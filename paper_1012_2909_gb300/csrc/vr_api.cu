@@ -43,6 +43,10 @@ struct vr_ctx {
     CUtensorMap tmap;
     bool has_tmap = false;
     vr_path path = VR_PATH_AUTO;
+    vr_tuning tune{8, 4, 128, 8};  // tile_w, tile_h, block, group
+    bool graph_mode = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
     // scratch
     int* work = nullptr;
     int work_slots = 0;
@@ -281,6 +285,8 @@ vr_status vr_destroy(vr_ctx* ctx) {
         if (ctx->krange) cudaFree(ctx->krange);
         if (ctx->enc) cudaFree(ctx->enc);
         if (ctx->tf_partials) cudaFree(ctx->tf_partials);
+        if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+        if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
         if (ctx->status_host) cudaFreeHost(ctx->status_host);
     }
     delete ctx;
@@ -485,12 +491,15 @@ vr_status render_ray(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
     P.width = ctx->cams[0].width;
     P.height = ctx->cams[0].height;
     P.mode = mode;
-    P.tiles_x = (P.width + kTileW - 1) / kTileW;
-    P.tiles_y = (P.height + kTileH - 1) / kTileH;
+    P.tile_w = ctx->tune.tile_w;
+    P.tile_h = ctx->tune.tile_h;
+    P.tiles_x = (P.width + P.tile_w - 1) / P.tile_w;
+    P.tiles_y = (P.height + P.tile_h - 1) / P.tile_h;
     P.step = ctx->opt.step;
     P.ert = (float)ctx->opt.ert;
     P.samples = ctx->sample_counter;
-    const int grid = ctx->num_sms * march_blocks_per_sm(ctx->dtype, mode);
+    const int block = ctx->tune.block;
+    const int grid = ctx->num_sms * march_blocks_per_sm(ctx->dtype, mode, block) * block / 32;
     const long long img = (long long)P.width * P.height;
     if (ctx->ev_start) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
     for (int b = 0; b < nbatch; ++b) {
@@ -500,8 +509,9 @@ vr_status render_ray(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
         P.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)c0 * img;
         P.out_max = (mode == VR_MIP && out_max) ? out_max + (long long)c0 * img : nullptr;
         P.work = ctx->work + b;
-        const int tiles = P.tiles_x * P.tiles_y * P.ncams;
-        VR_CK(launch_march(P, ctx->dtype, std::min(grid, tiles), s), "vr_render: march launch");
+        const int tiles = P.tiles_x * P.tiles_y * P.ncams;  // one warp per tile
+        const int blocks = std::max(1, std::min(grid / (block / 32), (tiles + block / 32 - 1) / (block / 32)));
+        VR_CK(launch_march(P, ctx->dtype, blocks, block, s), "vr_render: march launch");
     }
     if (ctx->ev_stop) VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
     return VR_OK;
@@ -568,7 +578,8 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
         bp.work = ctx->work + kMaxLaunchCams + (c0 / per) % 4096;
         VR_CK(cudaMemsetAsync(bp.work, 0, sizeof(int), s), "vr_render: scheduler reset");
         if (c0 == 0 && ctx->ev_start) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
-        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, grid, ctx->cells, s), "vr_render: brick pass");
+        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, grid, ctx->cells, s, ctx->tune.group),
+              "vr_render: brick pass");
         if (c0 + nb >= ncams && ctx->ev_stop) VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
         for (int i = 0; i < nb; ++i) {
             pp.cam = ctx->cams[(size_t)(c0 + i)];
@@ -655,7 +666,8 @@ vr_status brick_mip_with_scratch(vr_ctx* ctx, float* out_rgba, float* out_max, c
         bp.out_enc = enc;
         VR_CK(cudaMemsetAsync(work, 0, sizeof(int), s), "scheduler reset");
         VR_CK(launch_pixel_setup(pp, s), "pixel set-up");
-        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, 2 * ctx->num_sms, ctx->cells, s), "brick pass");
+        VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, 2 * ctx->num_sms, ctx->cells, s, ctx->tune.group),
+              "brick pass");
         VR_CK(launch_mip_finalize(pp, s), "finalise");
     }
     return VR_OK;
@@ -673,8 +685,30 @@ vr_status vr_set_path(vr_ctx* ctx, vr_path path) {
     return VR_OK;
 }
 
-vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, void* stream) {
-    if (!ctx) return VR_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+vr_path resolve_path(const vr_ctx* ctx, vr_mode mode) {
+    vr_path path = ctx->path;
+    if (path == VR_PATH_AUTO) path = (mode == VR_MIP && ctx->has_tmap) ? VR_PATH_BRICK : VR_PATH_RAY;
+    return path;
+}
+
+// The launches of one render on stream s (no allocation: scratch is sized first).
+vr_status render_dispatch(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, cudaStream_t s) {
+    const vr_path path = resolve_path(ctx, mode);
+    if (path == VR_PATH_BRICK) {
+        if (mode != VR_MIP)
+            return fail(ctx, VR_ERR_UNSUPPORTED, "vr_render: the brick path renders VR_MIP only");
+        if (!ctx->has_tmap)
+            return fail(ctx, VR_ERR_UNSUPPORTED, "vr_render: the brick path needs bricks of at least 32 voxels");
+        return render_brick_mip(ctx, out_rgba, out_max, s);
+    }
+    return render_ray(ctx, mode, out_rgba, out_max, s);
+}
+
+vr_status render_checks(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max) {
     if (mode != VR_COMPOSITE && mode != VR_MIP) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: bad mode");
     if (!out_rgba) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: out_rgba is NULL");
     if (reinterpret_cast<uintptr_t>(out_rgba) % 16 || reinterpret_cast<uintptr_t>(out_max) % 4)
@@ -686,22 +720,153 @@ vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, 
         const int code = *ctx->status_host;
         *ctx->status_host = 0;
         return fail(ctx, VR_ERR_INTERNAL,
-                    "an earlier brick pass stopped: a shared-memory load wait exceeded its bound (status " +
+                    "an earlier device pass stopped: a bounded wait expired or a limit was hit (status " +
                         std::to_string(code) + ")");
     }
+    return VR_OK;
+}
+
+// Graph mode: capture the render's launches on a private stream, update (or
+// instantiate) the cached executable graph, launch it on the caller's stream.
+// Camera, table and output changes reach the graph through the update.
+vr_status render_graphed(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, cudaStream_t s) {
+    if (resolve_path(ctx, mode) == VR_PATH_BRICK) {
+        const long long img = (long long)ctx->cams[0].width * ctx->cams[0].height;
+        vr_status st = ensure_pixel_scratch(ctx, img * std::min((int)ctx->cams.size(), kMaxLaunchCams));
+        if (st != VR_OK) return st;
+    }
+    if (!ctx->cap_stream)
+        VR_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "vr_render: capture stream");
+    // the capture stream must see the caller's earlier work before the graph runs;
+    // the graph itself is launched on s, so only the capture is on cap_stream
+    cudaEvent_t saved_start = ctx->ev_start, saved_stop = ctx->ev_stop;
+    ctx->ev_start = ctx->ev_stop = nullptr;  // profiling events are not recorded in graph mode
+    VR_CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "vr_render: begin capture");
+    vr_status st = render_dispatch(ctx, mode, out_rgba, out_max, ctx->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    ctx->ev_start = saved_start;
+    ctx->ev_stop = saved_stop;
+    if (st != VR_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "vr_render: end capture");
+    if (ctx->graph_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(ctx->graph_exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(ctx->graph_exec);
+            ctx->graph_exec = nullptr;
+        }
+    }
+    if (!ctx->graph_exec) {
+        e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            ctx->graph_exec = nullptr;
+            return cuda_fail(ctx, e, "vr_render: graph instantiate");
+        }
+    }
+    cudaGraphDestroy(graph);
+    VR_CK(cudaGraphLaunch(ctx->graph_exec, s), "vr_render: graph launch");
+    return VR_OK;
+}
+
+bool tuning_ok(const vr_tuning& t) {
+    const bool tile = t.tile_w > 0 && t.tile_h > 0 && t.tile_w * t.tile_h == 32;
+    const bool block = t.block == 64 || t.block == 128 || t.block == 256;
+    const bool group = t.group == 4 || t.group == 8 || t.group == 16;
+    return tile && block && group;
+}
+
+}  // namespace
+
+extern "C" {
+
+vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, void* stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    vr_status st = render_checks(ctx, mode, out_rgba, out_max);
+    if (st != VR_OK) return st;
     DevGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VR_CK(cudaGetLastError(), "vr_render: pending CUDA error");
-    vr_path path = ctx->path;
-    if (path == VR_PATH_AUTO) path = (mode == VR_MIP && ctx->has_tmap) ? VR_PATH_BRICK : VR_PATH_RAY;
-    if (path == VR_PATH_BRICK) {
-        if (mode != VR_MIP)
-            return fail(ctx, VR_ERR_UNSUPPORTED, "vr_render: the brick path renders VR_MIP only");
-        if (!ctx->has_tmap)
-            return fail(ctx, VR_ERR_UNSUPPORTED, "vr_render: the brick path needs bricks of at least 32 voxels");
-        return render_brick_mip(ctx, out_rgba, out_max, s);
+    if (ctx->graph_mode) return render_graphed(ctx, mode, out_rgba, out_max, s);
+    return render_dispatch(ctx, mode, out_rgba, out_max, s);
+}
+
+vr_status vr_set_graph(vr_ctx* ctx, int enable) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    ctx->graph_mode = enable != 0;
+    return VR_OK;
+}
+
+vr_status vr_get_tuning(const vr_ctx* ctx, vr_tuning* out) {
+    if (!ctx || !out) return VR_ERR_INVALID_ARG;
+    *out = ctx->tune;
+    return VR_OK;
+}
+
+vr_status vr_set_tuning(vr_ctx* ctx, const vr_tuning* t) {
+    if (!ctx || !t) return VR_ERR_INVALID_ARG;
+    if (!tuning_ok(*t))
+        return fail(ctx, VR_ERR_INVALID_ARG,
+                    "vr_set_tuning: need tile_w * tile_h == 32, block in {64,128,256}, group in {4,8,16}");
+    ctx->tune = *t;
+    return VR_OK;
+}
+
+vr_status vr_autotune(vr_ctx* ctx, vr_mode mode, float* scratch_rgba, int reps, vr_tuning* best,
+                      double* best_ms, void* stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (reps < 1 || reps > 1000) return fail(ctx, VR_ERR_INVALID_ARG, "vr_autotune: reps in [1, 1000]");
+    vr_status st = render_checks(ctx, mode, scratch_rgba, nullptr);
+    if (st != VR_OK) return st;
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<vr_tuning> cands;
+    const vr_tuning base = ctx->tune;
+    if (resolve_path(ctx, mode) == VR_PATH_BRICK) {
+        for (int grp : {4, 8, 16}) cands.push_back(vr_tuning{base.tile_w, base.tile_h, base.block, grp});
+    } else {
+        const int tiles[5][2] = {{8, 4}, {4, 8}, {16, 2}, {2, 16}, {32, 1}};
+        for (auto& t : tiles)
+            for (int blk : {64, 128, 256}) cands.push_back(vr_tuning{t[0], t[1], blk, base.group});
     }
-    return render_ray(ctx, mode, out_rgba, out_max, s);
+    cudaEvent_t e0, e1;
+    VR_CK(cudaEventCreate(&e0), "vr_autotune: event");
+    VR_CK(cudaEventCreate(&e1), "vr_autotune: event");
+    const bool saved_graph = ctx->graph_mode;
+    ctx->graph_mode = false;
+    double best_t = 1e300;
+    vr_tuning best_c = base;
+    for (const vr_tuning& c : cands) {
+        ctx->tune = c;
+        st = render_dispatch(ctx, mode, scratch_rgba, nullptr, s);  // warm-up
+        if (st != VR_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == VR_OK; ++r) st = render_dispatch(ctx, mode, scratch_rgba, nullptr, s);
+        cudaEventRecord(e1, s);
+        if (st != VR_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = cuda_fail(ctx, cudaGetLastError(), "vr_autotune: timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / reps < best_t) {
+            best_t = ms / reps;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->graph_mode = saved_graph;
+    ctx->tune = (st == VR_OK) ? best_c : base;
+    if (st != VR_OK) return st;
+    if (best) *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    return VR_OK;
 }
 
 vr_status vr_render_backward(vr_ctx* ctx, vr_mode mode, const float* dL_dimg, float* dL_dtf, float* dL_dvol,

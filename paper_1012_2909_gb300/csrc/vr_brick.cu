@@ -28,14 +28,7 @@ namespace {
 
 constexpr int kBrickThreads = 256;  // two CTAs per SM
 constexpr int kSegCap = 512;        // segment records per chunk
-#ifndef VR_BRICK_GROUP
-#define VR_BRICK_GROUP 8
-#endif
-constexpr int kGroup = VR_BRICK_GROUP;  // lanes per segment in the march
-#ifndef VR_BRICK_UNROLL
-#define VR_BRICK_UNROLL 1
-#endif
-constexpr int kUnroll = VR_BRICK_UNROLL;  // samples per lane per step
+constexpr int kUnroll = 1;  // samples per lane per step (more overlap measured slower)
 
 template <typename T> struct Cell;
 template <> struct Cell<float> {
@@ -411,7 +404,7 @@ __device__ __forceinline__ void march_segments(const BrickParams& P, const T* ti
 // rectangles into segment records, and the other CTA of the SM marches.  A
 // staged cell serves every camera of the launch (the 25 panels of a wall are
 // rendered from one pass over the cube).
-template <typename T, bool ONE>
+template <typename T, bool ONE, int GROUP>
 __global__ void __launch_bounds__(kBrickThreads, 2)
 k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BrickParams P,
             const CellDesc* __restrict__ list, const int* __restrict__ count) {
@@ -497,7 +490,7 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     for (;;) {
         const int nseg = s_cnt[chunk & 1];
         if (tid == 0) s_cnt[(chunk + 1) & 1] = 0;
-        march_segments<T, kGroup, kUnroll>(P, tile, segs, nseg, warp, lane);
+        march_segments<T, GROUP, kUnroll>(P, tile, segs, nseg, warp, lane);
         __syncthreads();
         ++chunk;
         c0 += kSegCap;
@@ -548,27 +541,35 @@ __global__ void k_mip_finalize(const __grid_constant__ PixelParams P) {
     }
 }
 
-template <typename T, bool ONE>
+template <typename T, bool ONE, int GROUP>
 cudaError_t launch_brick(const void* tmap, const BrickParams& p, int grid, const CellDesc* list, const int* count,
                          cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_brick_mip<T, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_brick_mip<T, ONE, GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          TileGeom<T>::SMEM);
     if (e != cudaSuccess) return e;
-    k_brick_mip<T, ONE><<<grid, kBrickThreads, TileGeom<T>::SMEM, s>>>(*static_cast<const CUtensorMap*>(tmap), p,
-                                                                       list, count);
+    k_brick_mip<T, ONE, GROUP><<<grid, kBrickThreads, TileGeom<T>::SMEM, s>>>(
+        *static_cast<const CUtensorMap*>(tmap), p, list, count);
     return cudaGetLastError();
 }
 
+template <typename T, int GROUP>
+cudaError_t launch_brick_g(const void* tmap, const BrickParams& p, int grid, const CellDesc* list,
+                           const int* count, cudaStream_t s) {
+    return p.ncams == 1 ? launch_brick<T, true, GROUP>(tmap, p, grid, list, count, s)
+                        : launch_brick<T, false, GROUP>(tmap, p, grid, list, count, s);
+}
+
 template <typename T>
-cudaError_t launch_t(const void* tmap, const BrickParams& p, int grid, void* cells, cudaStream_t s) {
+cudaError_t launch_t(const void* tmap, const BrickParams& p, int grid, void* cells, cudaStream_t s, int group) {
     CellDesc* list = reinterpret_cast<CellDesc*>(static_cast<char*>(cells) + 256);
     int* count = static_cast<int*>(cells);
     const int nunits = p.nbricks * p.ncells_x * p.ncells_y * p.ncells_z;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     k_cell_list<T><<<std::min((nunits + 255) / 256, 4096), 256, 0, s>>>(p, list, count);
-    return p.ncams == 1 ? launch_brick<T, true>(tmap, p, grid, list, count, s)
-                        : launch_brick<T, false>(tmap, p, grid, list, count, s);
+    if (group == 4) return launch_brick_g<T, 4>(tmap, p, grid, list, count, s);
+    if (group == 16) return launch_brick_g<T, 16>(tmap, p, grid, list, count, s);
+    return launch_brick_g<T, 8>(tmap, p, grid, list, count, s);
 }
 
 }  // namespace
@@ -614,10 +615,10 @@ cudaError_t launch_mip_finalize(const PixelParams& p, cudaStream_t s) {
 size_t brick_cells_bytes(long long nunits) { return 256 + (size_t)nunits * sizeof(CellDesc); }
 
 cudaError_t launch_brick_mip(const void* tmap, const BrickParams& p, vr_dtype dt, int grid, void* cells,
-                             cudaStream_t s) {
-    if (dt == VR_F32) return launch_t<float>(tmap, p, grid, cells, s);
-    if (dt == VR_F16) return launch_t<__half>(tmap, p, grid, cells, s);
-    return launch_t<__nv_bfloat16>(tmap, p, grid, cells, s);
+                             cudaStream_t s, int group) {
+    if (dt == VR_F32) return launch_t<float>(tmap, p, grid, cells, s, group);
+    if (dt == VR_F16) return launch_t<__half>(tmap, p, grid, cells, s, group);
+    return launch_t<__nv_bfloat16>(tmap, p, grid, cells, s, group);
 }
 
 }  // namespace vr

@@ -50,7 +50,7 @@ struct MarchParams {
     CamDev cams[kMaxLaunchCams];
     int ncams, width, height, mode;
     int tiles_x, tiles_y;
-    int pad0, pad1;
+    int tile_w, tile_h;          // pixels of one warp work item (tile_w * tile_h == 32)
     double step;
     float ert;
     int pad2;
@@ -124,14 +124,14 @@ struct PixelParams {
 cudaError_t launch_repack(const float* src, long long src_z0, long long src_planes, int bz,
                           const VolDev& v, vr_dtype dt, void* pool, unsigned int* minmax,
                           cudaStream_t s);
-cudaError_t launch_march(const MarchParams& p, vr_dtype dt, int grid, cudaStream_t s);
-int march_blocks_per_sm(vr_dtype dt, int mode);
+cudaError_t launch_march(const MarchParams& p, vr_dtype dt, int grid, int block, cudaStream_t s);
+int march_blocks_per_sm(vr_dtype dt, int mode, int block);
 cudaError_t launch_pixel_setup(const PixelParams& p, cudaStream_t s);
 cudaError_t launch_mip_finalize(const PixelParams& p, cudaStream_t s);
 // `cells` is per-context scratch of brick_cells_bytes(units) bytes (a counter and the
 // per-view list of cells with work); the brick kernel's work counter is p.work.
 cudaError_t launch_brick_mip(const void* tmap, const BrickParams& p, vr_dtype dt, int grid, void* cells,
-                             cudaStream_t s);
+                             cudaStream_t s, int group = 8);
 size_t brick_cells_bytes(long long nunits);
 // Cell (staging unit) edge lengths for a storage type; the brick edge must be a
 // multiple of each.

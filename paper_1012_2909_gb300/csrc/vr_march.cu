@@ -16,7 +16,7 @@ namespace {
 constexpr int kSegCap = 128;  // samples between double-precision re-anchors
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kMarchThreads)
+__global__ void __launch_bounds__(256)
 k_march(const __grid_constant__ MarchParams P) {
     __shared__ float4 s_tf[kMaxTF];
     for (int i = threadIdx.x; i < P.tf.n; i += blockDim.x) s_tf[i] = P.tf.tab[i];
@@ -37,8 +37,8 @@ k_march(const __grid_constant__ MarchParams P) {
         const int cam = item / tiles_per_cam;
         const int tile = item - cam * tiles_per_cam;
         const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
-        const int px = tx * kTileW + (lane % kTileW);
-        const int py = ty * kTileH + (lane / kTileW);
+        const int px = tx * P.tile_w + (lane % P.tile_w);
+        const int py = ty * P.tile_h + (lane / P.tile_w);
         if (px >= P.width || py >= P.height) continue;  // ragged edge tile; the lane
                                                         // rejoins at the next shuffle
         const CamDev& C = P.cams[cam];
@@ -108,17 +108,16 @@ void* pick(vr_dtype dt, int mode) {
 
 }  // namespace
 
-int march_blocks_per_sm(vr_dtype dt, int mode) {
+int march_blocks_per_sm(vr_dtype dt, int mode, int block) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(dt, mode), kMarchThreads, 0) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(dt, mode), block, 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_march(const MarchParams& p, vr_dtype dt, int grid, cudaStream_t s) {
+cudaError_t launch_march(const MarchParams& p, vr_dtype dt, int grid, int block, cudaStream_t s) {
     void* args[] = {const_cast<MarchParams*>(&p)};
-    return cudaLaunchKernel(pick(dt, p.mode), dim3(grid), dim3(kMarchThreads), args, 0, s);
+    return cudaLaunchKernel(pick(dt, p.mode), dim3(grid), dim3(block), args, 0, s);
 }
 
 }  // namespace vr
