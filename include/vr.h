@@ -66,9 +66,28 @@ typedef enum { VR_COMPOSITE = 0, VR_MIP = 1 } vr_mode;
  *   memory in 32^3 cells (TMA-staged) and every ray segment crossing a cell is
  *   marched there; partial results are folded per pixel.  VR_MIP only; needs
  *   bricks of at least 32 voxels.
+ * VR_PATH_SORTLAST: the paper's decomposition into parts rendered apart and
+ *   combined.  Composite: every brick renders a partial image (C, T) of the
+ *   samples it owns, starting from T = 1, on its screen footprint, and the
+ *   partial images are folded per pixel front to back in visibility order
+ *   (ascending sum |b - e| over axes, e the eye's brick; sign-weighted brick
+ *   sum for orthographic views).  Early termination does not apply: the result
+ *   is the composite with ert disabled.  VR_MIP: as VR_PATH_BRICK.
+ * VR_PATH_LAYERED: composite by bricks, one visibility layer per launch, each
+ *   pixel's running (C, T) carried from layer to layer with per-sample early
+ *   termination (the same image as VR_PATH_RAY); bricks of terminated pixels
+ *   are skipped.  VR_MIP: as VR_PATH_BRICK.
+ * Both read back per-view layer sizes (a host synchronisation), so graph mode
+ * does not apply to them.
  * VR_PATH_AUTO (default): VR_PATH_BRICK for VR_MIP when available, else
  *   VR_PATH_RAY.  Every path computes the same discretisation. */
-typedef enum { VR_PATH_AUTO = 0, VR_PATH_RAY = 1, VR_PATH_BRICK = 2 } vr_path;
+typedef enum {
+    VR_PATH_AUTO = 0,
+    VR_PATH_RAY = 1,
+    VR_PATH_BRICK = 2,
+    VR_PATH_SORTLAST = 3,
+    VR_PATH_LAYERED = 4
+} vr_path;
 
 /*
  * Camera.  Pixel (px, py), py = 0 the top row, has window coordinates

@@ -28,8 +28,9 @@ VR_F32, VR_F16, VR_BF16 = 0, 1, 2
 VR_COMPOSITE, VR_MIP = 0, 1
 DTYPES = {"f32": VR_F32, "f16": VR_F16, "bf16": VR_BF16}
 MODES = {"composite": VR_COMPOSITE, "mip": VR_MIP}
-VR_PATH_AUTO, VR_PATH_RAY, VR_PATH_BRICK = 0, 1, 2
-PATHS = {"auto": VR_PATH_AUTO, "ray": VR_PATH_RAY, "brick": VR_PATH_BRICK}
+VR_PATH_AUTO, VR_PATH_RAY, VR_PATH_BRICK, VR_PATH_SORTLAST, VR_PATH_LAYERED = 0, 1, 2, 3, 4
+PATHS = {"auto": VR_PATH_AUTO, "ray": VR_PATH_RAY, "brick": VR_PATH_BRICK, "sortlast": VR_PATH_SORTLAST,
+         "layered": VR_PATH_LAYERED}
 
 
 class VrError(RuntimeError):

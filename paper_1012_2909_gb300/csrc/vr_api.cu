@@ -53,6 +53,20 @@ struct vr_ctx {
     int2* krange = nullptr;        // per-pixel sample range of the brick pass
     unsigned int* enc = nullptr;   // per-pixel running maximum when out_max is NULL
     long long scratch_pix = 0;
+    // sort-last / layered scratch
+    BrickFoot* foot = nullptr;
+    int* order = nullptr;
+    int* tile_start = nullptr;
+    long long sort_bricks = 0;
+    int* layer_buf = nullptr;      // count | start | fill
+    int layer_cap = 0;
+    unsigned long long* partial_used = nullptr;
+    float4* partial = nullptr;
+    long long partial_cap = 0;
+    float4* state = nullptr;
+    long long state_cap = 0;
+    int* host_rb = nullptr;        // page-locked read-back buffer
+    int host_rb_cap = 0;
     float* tf_partials = nullptr;  // adjoint: per-block table-gradient partials
     size_t tf_partials_n = 0;
     int* status_host = nullptr;    // mapped, page-locked device status word
@@ -285,6 +299,10 @@ vr_status vr_destroy(vr_ctx* ctx) {
         if (ctx->krange) cudaFree(ctx->krange);
         if (ctx->enc) cudaFree(ctx->enc);
         if (ctx->tf_partials) cudaFree(ctx->tf_partials);
+        for (void* p : {(void*)ctx->foot, (void*)ctx->order, (void*)ctx->tile_start, (void*)ctx->layer_buf,
+                        (void*)ctx->partial_used, (void*)ctx->partial, (void*)ctx->state})
+            if (p) cudaFree(p);
+        if (ctx->host_rb) cudaFreeHost(ctx->host_rb);
         if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
         if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
         if (ctx->status_host) cudaFreeHost(ctx->status_host);
@@ -592,6 +610,150 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
     return VR_OK;
 }
 
+// grow a device buffer to at least n elements (contents not kept)
+template <typename P>
+vr_status grow(vr_ctx* ctx, P*& ptr, long long& cap, long long n, const char* what) {
+    if (n <= cap) return VR_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    VR_CK(cudaMalloc(&ptr, sizeof(P) * (size_t)n), what);
+    cap = n;
+    return VR_OK;
+}
+
+// Upper bound of the visibility key of any brick for this camera, plus one.
+int layer_bound(const vr_ctx* ctx, const CamDev& c) {
+    const int nb[3] = {ctx->nbx, ctx->nby, ctx->nbz};
+    int m = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (c.type == 1) {
+            const long long e = (long long)std::floor(c.eye[a] / (double)ctx->B);
+            m += (int)std::min<long long>(1 << 20, std::max(std::llabs(e), std::llabs((long long)nb[a] - 1 - e)));
+        } else {
+            m += nb[a] - 1;
+        }
+    }
+    return m + 1;
+}
+
+// Composite in object order.  carried = false: per-brick partial images from
+// T = 1 folded in visibility order (no early termination).  carried = true:
+// one visibility layer of bricks per launch, each pixel's running (C, T)
+// carried through with per-sample early termination.
+vr_status render_bricks_composite(vr_ctx* ctx, float* out_rgba, cudaStream_t s, bool carried) {
+    const int W = ctx->cams[0].width, H = ctx->cams[0].height;
+    const long long img = (long long)W * H;
+    const long long nbricks = (long long)ctx->nbx * ctx->nby * ctx->nbz;
+    vr_status st = ensure_pixel_scratch(ctx, img);
+    if (st != VR_OK) return st;
+    long long cap = ctx->sort_bricks;
+    if (nbricks + 1 > cap) {
+        if (ctx->foot) cudaFree(ctx->foot);
+        if (ctx->order) cudaFree(ctx->order);
+        if (ctx->tile_start) cudaFree(ctx->tile_start);
+        ctx->foot = nullptr;
+        ctx->order = nullptr;
+        ctx->tile_start = nullptr;
+        ctx->sort_bricks = 0;
+        VR_CK(cudaMalloc(&ctx->foot, sizeof(BrickFoot) * (size_t)nbricks), "sort-last scratch");
+        VR_CK(cudaMalloc(&ctx->order, sizeof(int) * (size_t)nbricks), "sort-last scratch");
+        VR_CK(cudaMalloc(&ctx->tile_start, sizeof(int) * (size_t)(nbricks + 1)), "sort-last scratch");
+        ctx->sort_bricks = nbricks + 1;
+    }
+    if (!ctx->partial_used) VR_CK(cudaMalloc(&ctx->partial_used, sizeof(unsigned long long)), "sort-last scratch");
+    if (carried) {
+        st = grow(ctx, ctx->state, ctx->state_cap, img, "layered state");
+        if (st != VR_OK) return st;
+    }
+    SortParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.vol = vol_dev(ctx);
+    sp.tf = tf_dev(ctx);
+    sp.step = (float)ctx->opt.step;
+    sp.ert = carried ? (float)ctx->opt.ert : 2.0f;
+    sp.krange = ctx->krange;
+    sp.foot = ctx->foot;
+    sp.order = ctx->order;
+    sp.tile_start = ctx->tile_start;
+    sp.partial_used = ctx->partial_used;
+    sp.state = ctx->state;
+    PixelParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.vol = sp.vol;
+    pp.tf = sp.tf;
+    pp.step = ctx->opt.step;
+    pp.width = W;
+    pp.height = H;
+    pp.krange = ctx->krange;
+    pp.enc = ctx->enc;
+    const int grid = ctx->num_sms * 8;
+    for (size_t ci = 0; ci < ctx->cams.size(); ++ci) {
+        const CamDev& cd = ctx->cams[ci];
+        if (!cam_ff(cd, sp.cam)) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: camera basis is singular");
+        const int L = layer_bound(ctx, cd);
+        for (int ax = 0; ax < 3; ++ax)
+            sp.eye_brick[ax] = (int)std::max<double>(-(1 << 20), std::min<double>(1 << 20, std::floor(cd.eye[ax] / (double)ctx->B)));
+        if (L + 1 > ctx->layer_cap) {
+            if (ctx->layer_buf) cudaFree(ctx->layer_buf);
+            ctx->layer_buf = nullptr;
+            ctx->layer_cap = 0;
+            VR_CK(cudaMalloc(&ctx->layer_buf, sizeof(int) * 3 * (size_t)(L + 1)), "sort-last scratch");
+            ctx->layer_cap = L + 1;
+        }
+        if (L + 2 > ctx->host_rb_cap) {
+            if (ctx->host_rb) cudaFreeHost(ctx->host_rb);
+            ctx->host_rb = nullptr;
+            ctx->host_rb_cap = 0;
+            VR_CK(cudaHostAlloc(&ctx->host_rb, sizeof(int) * (size_t)(L + 4), cudaHostAllocDefault), "read-back");
+            ctx->host_rb_cap = L + 4;
+        }
+        sp.max_layers = L;
+        sp.layer_count = ctx->layer_buf;
+        sp.layer_start = ctx->layer_buf + (L + 1);
+        sp.layer_fill = ctx->layer_buf + 2 * (L + 1);
+        sp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)ci * img;
+        pp.cam = cd;
+        VR_CK(launch_pixel_setup(pp, s), "vr_render: pixel set-up");
+        VR_CK(cudaMemsetAsync(sp.layer_count, 0, sizeof(int) * (size_t)L, s), "vr_render: reset");
+        VR_CK(cudaMemsetAsync(sp.partial_used, 0, sizeof(unsigned long long), s), "vr_render: reset");
+        VR_CK(launch_brick_footprints(sp, s), "vr_render: brick footprints");
+        // read back the layer starts and the partial-image size (host decides the launches)
+        VR_CK(cudaMemcpyAsync(ctx->host_rb, sp.layer_start, sizeof(int) * (size_t)(L + 1), cudaMemcpyDeviceToHost, s),
+              "vr_render: read-back");
+        unsigned long long used = 0;
+        VR_CK(cudaMemcpyAsync(&used, sp.partial_used, sizeof(used), cudaMemcpyDeviceToHost, s), "vr_render: read-back");
+        VR_CK(cudaStreamSynchronize(s), "vr_render: read-back");
+        if (!carried) {
+            vr_status g = grow(ctx, ctx->partial, ctx->partial_cap, (long long)std::max<unsigned long long>(used, 1),
+                               "partial images");
+            if (g != VR_OK) return g;
+            sp.partial = ctx->partial;
+            sp.work = ctx->work;
+            VR_CK(cudaMemsetAsync(sp.work, 0, sizeof(int), s), "vr_render: scheduler reset");
+            if (ctx->ev_start && ci == 0) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
+            VR_CK(launch_brick_partial(sp, ctx->dtype, false, 0, L, grid, s), "vr_render: partial images");
+            if (ctx->ev_stop && ci + 1 == ctx->cams.size())
+                VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
+            VR_CK(launch_sortlast_fold(sp, s), "vr_render: sort-last fold");
+        } else {
+            VR_CK(launch_state_init(sp, s), "vr_render: state init");
+            int slot = 0;
+            if (ctx->ev_start && ci == 0) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
+            for (int l = 0; l < L; ++l) {
+                if (ctx->host_rb[l + 1] == ctx->host_rb[l]) continue;  // empty layer
+                sp.work = ctx->work + (slot++ % ctx->work_slots);
+                VR_CK(cudaMemsetAsync(sp.work, 0, sizeof(int), s), "vr_render: scheduler reset");
+                VR_CK(launch_brick_partial(sp, ctx->dtype, true, l, l + 1, grid, s), "vr_render: layer");
+            }
+            if (ctx->ev_stop && ci + 1 == ctx->cams.size())
+                VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
+            VR_CK(launch_state_finish(sp, s), "vr_render: state finish");
+        }
+    }
+    return VR_OK;
+}
+
 }  // namespace
 
 namespace vr {
@@ -679,7 +841,8 @@ extern "C" {
 
 vr_status vr_set_path(vr_ctx* ctx, vr_path path) {
     if (!ctx) return VR_ERR_INVALID_ARG;
-    if (path != VR_PATH_AUTO && path != VR_PATH_RAY && path != VR_PATH_BRICK)
+    if (path != VR_PATH_AUTO && path != VR_PATH_RAY && path != VR_PATH_BRICK && path != VR_PATH_SORTLAST &&
+        path != VR_PATH_LAYERED)
         return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_path: unknown path");
     ctx->path = path;
     return VR_OK;
@@ -697,7 +860,10 @@ vr_path resolve_path(const vr_ctx* ctx, vr_mode mode) {
 
 // The launches of one render on stream s (no allocation: scratch is sized first).
 vr_status render_dispatch(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, cudaStream_t s) {
-    const vr_path path = resolve_path(ctx, mode);
+    vr_path path = resolve_path(ctx, mode);
+    if ((path == VR_PATH_SORTLAST || path == VR_PATH_LAYERED) && mode == VR_COMPOSITE)
+        return render_bricks_composite(ctx, out_rgba, s, path == VR_PATH_LAYERED);
+    if (path == VR_PATH_SORTLAST || path == VR_PATH_LAYERED) path = VR_PATH_BRICK;  // MIP: order-free
     if (path == VR_PATH_BRICK) {
         if (mode != VR_MIP)
             return fail(ctx, VR_ERR_UNSUPPORTED, "vr_render: the brick path renders VR_MIP only");
@@ -791,7 +957,9 @@ vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, 
     DevGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VR_CK(cudaGetLastError(), "vr_render: pending CUDA error");
-    if (ctx->graph_mode) return render_graphed(ctx, mode, out_rgba, out_max, s);
+    const vr_path path = resolve_path(ctx, mode);
+    const bool host_steered = (path == VR_PATH_SORTLAST || path == VR_PATH_LAYERED) && mode == VR_COMPOSITE;
+    if (ctx->graph_mode && !host_steered) return render_graphed(ctx, mode, out_rgba, out_max, s);
     return render_dispatch(ctx, mode, out_rgba, out_max, s);
 }
 

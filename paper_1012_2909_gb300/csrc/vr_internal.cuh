@@ -107,6 +107,36 @@ struct AdjParams {
     int* status;          // device status word
 };
 
+// Screen footprint of one brick for the sort-last paths.
+struct BrickFoot {
+    int4 rect;          // pixel rectangle (empty: x > z)
+    int key;            // visibility layer
+    int pad;
+    long long offset;   // first pixel of its partial image
+};
+
+// Launch parameters of the sort-last / layered paths (one camera).
+struct SortParams {
+    VolDev vol;
+    TFDev tf;
+    CamFF cam;
+    float step, ert;
+    int max_layers, pad;
+    int eye_brick[3], pad2;           // floor(eye / B) (perspective visibility keys)
+    const int2* krange;
+    BrickFoot* foot;                  // per brick
+    int* order;                       // visible bricks grouped by layer
+    int* layer_count;                 // max_layers
+    int* layer_start;                 // max_layers + 1
+    int* layer_fill;                  // max_layers
+    int* tile_start;                  // nbricks + 1
+    unsigned long long* partial_used; // pixels handed out to partial images
+    float4* partial;                  // partial images (C, T)
+    float4* state;                    // running (C, T) per pixel (layered path)
+    float4* out_rgba;
+    int* work;                        // zeroed work counter of a launch
+};
+
 // Per-pixel set-up and finalisation around the brick pass.
 struct PixelParams {
     VolDev vol;
@@ -139,6 +169,12 @@ void brick_cell_dims(vr_dtype dt, int* cx, int* cy, int* cz);
 // TMA box of one cell (cell + 2 ghost, x padded to 16 bytes), in elements.
 void brick_box_dims(vr_dtype dt, int* bx, int* by, int* bz);
 constexpr int kMarchThreads = 128;
+cudaError_t launch_brick_footprints(const SortParams& p, cudaStream_t s);
+cudaError_t launch_brick_partial(const SortParams& p, vr_dtype dt, bool carried, int l0, int l1, int grid,
+                                 cudaStream_t s);
+cudaError_t launch_sortlast_fold(const SortParams& p, cudaStream_t s);
+cudaError_t launch_state_init(const SortParams& p, cudaStream_t s);
+cudaError_t launch_state_finish(const SortParams& p, cudaStream_t s);
 int adjoint_threads();
 int adjoint_blocks_per_sm(vr_dtype dt, int mode, int ntf);
 cudaError_t launch_adjoint(const AdjParams& p, vr_dtype dt, int grid, cudaStream_t s);

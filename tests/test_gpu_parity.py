@@ -284,3 +284,26 @@ def test_wall_25_frusta_one_launch(vr, storage):
         for i in (0, 7, 24):
             compare(img[i].reshape(-1, 4), sc, panels[i], mode, tol=1e-4,
                     gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_sortlast_and_layered_composite(vr, storage):
+    """Object-order composite: per-brick partial images folded in visibility order equal
+    the oracle's composite without termination; the layered form (running state carried
+    from layer to layer) equals the oracle's composite with termination."""
+    for dims, brick in (((96, 80, 72), 32), ((45, 37, 29), 16), ((130, 70, 200), 64)):
+        p = synth.cube_params(*dims, seed=sum(dims) + 1, nsrc=8, ripple=True, ripple_period=32.0)
+        vol = synth.generate(p)
+        tf = synth.viridis_ramp_tf()
+        cams = [synth.orbit_view(dims, az, 53, 41) for az in (0.0, 47.0, 160.0, 290.0)]
+        cams += [synth.ortho_view(dims, 53, 41, rx_deg=-25.0, ry_deg=70.0),
+                 synth.look_at(dims, (0.1, -0.4, 1.0), 53, 41, dist_factor=0.3)]  # eye inside
+        rounded = oracle.round_storage(vol, storage)
+        sc_off = oracle.Scene(rounded, tf, -1.0, 20.0, 0.5, 2.0)
+        sc_on = oracle.Scene(rounded, tf, -1.0, 20.0, 0.5, 0.99)
+        img, _ = _render(vr, vol, tf, cams, "composite", storage=storage, brick=brick, path="sortlast")
+        for i, c in enumerate(cams):
+            compare(img[i].reshape(-1, 4), sc_off, c, "composite", tol=1e-4)
+        img, _ = _render(vr, vol, tf, cams, "composite", storage=storage, brick=brick, path="layered")
+        for i, c in enumerate(cams):
+            compare(img[i].reshape(-1, 4), sc_on, c, "composite", tol=1e-4)
