@@ -295,6 +295,42 @@ vr_status vr_set_kernel_events(vr_ctx* ctx, void* start, void* stop);
 #define VR_NOALLOC_MAX_PIXELS (1 << 21)
 vr_status vr_render_mip_noalloc(vr_ctx* ctx, float* out_rgba, float* out_max, void* stream);
 
+/*
+ * Out-of-core cubes (Abstract, Sec. 1: cubes larger than one machine's memory).
+ * The cube is never held whole: bricks are produced on demand by a caller
+ * callback, copied through page-locked staging (double-buffered) on a side
+ * stream into a fixed HBM brick cache of `cache_bytes`, evicted least recently
+ * used, and the render waits on CUDA events for the bricks it needs.
+ *   VR_MIP renders the visible bricks in cache-sized batches (maxima folded
+ *     across batches);
+ *   VR_COMPOSITE renders layer by layer in visibility order with each pixel's
+ *     running (C, T) carried and per-sample early termination; a brick whose
+ *     every footprint pixel has terminated is neither fetched nor rendered.
+ * The callback fills dst (float32, x fastest) with the cube values of the
+ * region [x0, x0+sx) x [y0, y0+sy) x [z0, z0+sz) and returns 0, or nonzero
+ * on failure (the render then returns VR_ERR_IO).  It is called from the
+ * thread that calls vr_render, one region at a time.
+ * Host waits (events, callbacks) are bounded by a deadline (default 120 s,
+ * vr_set_stream_timeout); on expiry the call returns VR_ERR_TIMEOUT and the
+ * context stays usable.  vr_render_backward and graph mode do not apply.
+ */
+typedef int (*vr_region_fn)(void* user, int64_t x0, int64_t y0, int64_t z0, int64_t sx,
+                            int64_t sy, int64_t sz, float* dst);
+
+typedef struct {
+    uint64_t bricks_fetched;  /* bricks produced and uploaded            */
+    uint64_t bricks_culled;   /* bricks skipped behind terminated rays    */
+    uint64_t bytes_h2d;       /* bytes copied host -> device              */
+    uint64_t batches;         /* render batches (cache fills)             */
+    double generate_s;        /* host time inside the callback            */
+    double wait_s;            /* host time waiting on device events       */
+} vr_stream_stats;
+
+vr_status vr_load_cube_streamed(vr_ctx* ctx, vr_region_fn fn, void* user, int64_t nx, int64_t ny,
+                                int64_t nz, vr_dtype storage, uint64_t cache_bytes);
+vr_status vr_get_stream_stats(const vr_ctx* ctx, vr_stream_stats* out);
+vr_status vr_set_stream_timeout(vr_ctx* ctx, double seconds);
+
 /* Layout of the loaded cube; VR_ERR_STATE if none is loaded. */
 vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info);
 

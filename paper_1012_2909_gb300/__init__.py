@@ -57,6 +57,17 @@ class vr_tuning(ctypes.Structure):
                 ("group", ctypes.c_int32)]
 
 
+class vr_stream_stats(ctypes.Structure):
+    _fields_ = [("bricks_fetched", ctypes.c_uint64), ("bricks_culled", ctypes.c_uint64),
+                ("bytes_h2d", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("generate_s", ctypes.c_double), ("wait_s", ctypes.c_double)]
+
+
+REGION_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.c_void_p)
+
+
 class vr_cube_info(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
                 ("nbx", ctypes.c_int32), ("nby", ctypes.c_int32), ("nbz", ctypes.c_int32),
@@ -78,6 +89,10 @@ SIGNATURES = {
     "vr_set_camera": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "vr_render": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "vr_set_path": (ctypes.c_int, [_P, ctypes.c_int]),
+    "vr_load_cube_streamed": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_uint64]),
+    "vr_get_stream_stats": (ctypes.c_int, [_P, _P]),
+    "vr_set_stream_timeout": (ctypes.c_int, [_P, ctypes.c_double]),
     "vr_get_tuning": (ctypes.c_int, [_P, _P]),
     "vr_set_tuning": (ctypes.c_int, [_P, _P]),
     "vr_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P]),
@@ -245,6 +260,29 @@ def vr_autotune(ctx, mode: str, scratch_rgba, reps: int = 5, stream=None, device
 
 def vr_set_graph(ctx, enable: bool = True):
     _check(ctx, load_library().vr_set_graph(ctx, int(bool(enable))), "vr_set_graph")
+
+
+def vr_load_cube_streamed(ctx, fn, user, dims, storage: str = "f16", cache_bytes: int = 1 << 30):
+    """Out-of-core cube of dims (nx, ny, nz) pulled on demand from the region callback
+    `fn` (a C function pointer as ctypes.c_void_p, or a REGION_FN) with `user` (a
+    ctypes object or address kept alive by the caller)."""
+    lib = load_library()
+    uptr = ctypes.c_void_p(ctypes.addressof(user)) if isinstance(user, ctypes.Structure) else user
+    fptr = ctypes.cast(fn, ctypes.c_void_p)
+    nx, ny, nz = dims
+    st = lib.vr_load_cube_streamed(ctx, fptr, uptr, int(nx), int(ny), int(nz), DTYPES[storage],
+                                   int(cache_bytes))
+    _check(ctx, st, "vr_load_cube_streamed")
+
+
+def vr_get_stream_stats(ctx) -> dict:
+    s = vr_stream_stats()
+    _check(ctx, load_library().vr_get_stream_stats(ctx, ctypes.byref(s)), "vr_get_stream_stats")
+    return {k: getattr(s, k) for k, _ in vr_stream_stats._fields_}
+
+
+def vr_set_stream_timeout(ctx, seconds: float):
+    _check(ctx, load_library().vr_set_stream_timeout(ctx, float(seconds)), "vr_set_stream_timeout")
 
 
 def vr_set_path(ctx, path: str = "auto"):

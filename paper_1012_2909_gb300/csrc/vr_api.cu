@@ -2,6 +2,8 @@
 // transfer function, cameras and render dispatch.  No exception crosses the
 // boundary; every failure becomes a vr_status with a message on the context.
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -33,6 +35,25 @@ struct vr_ctx {
     int* table = nullptr;
     unsigned int* minmax = nullptr;
     void* cells = nullptr;   // brick-pass cell list of the current view
+    long long pool_slots = 0; // slots of the brick store (all bricks in core, the cache out of core)
+    // out-of-core streaming
+    bool ooc = false;
+    vr_region_fn ooc_fn = nullptr;
+    void* ooc_user = nullptr;
+    std::vector<int> slot_brick, table_host;
+    std::vector<long long> slot_use;
+    long long ooc_tick = 0;
+    float* ooc_pin[2] = {nullptr, nullptr};
+    float* ooc_dev[2] = {nullptr, nullptr};
+    int* ooc_pin_table = nullptr;
+    int* ooc_pin_list = nullptr;
+    int* ooc_dev_list = nullptr;
+    cudaEvent_t ooc_ev[2] = {nullptr, nullptr};
+    cudaEvent_t ooc_ev_table = nullptr, ooc_ev_render = nullptr;
+    cudaStream_t ooc_side = nullptr;
+    int ooc_next_buf = 0;
+    double ooc_timeout_s = 120.0;
+    vr_stream_stats ooc_stats{};
     // transfer function
     bool has_tf = false;
     std::vector<float4> tf;
@@ -105,7 +126,35 @@ vr_status cuda_fail(vr_ctx* c, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
     } while (0)
 
+void free_ooc(vr_ctx* c) {
+    if (c->ooc_side) cudaStreamSynchronize(c->ooc_side);
+    for (int i = 0; i < 2; ++i) {
+        if (c->ooc_pin[i]) cudaFreeHost(c->ooc_pin[i]);
+        if (c->ooc_dev[i]) cudaFree(c->ooc_dev[i]);
+        if (c->ooc_ev[i]) cudaEventDestroy(c->ooc_ev[i]);
+        c->ooc_pin[i] = nullptr;
+        c->ooc_dev[i] = nullptr;
+        c->ooc_ev[i] = nullptr;
+    }
+    if (c->ooc_pin_table) cudaFreeHost(c->ooc_pin_table);
+    if (c->ooc_pin_list) cudaFreeHost(c->ooc_pin_list);
+    if (c->ooc_dev_list) cudaFree(c->ooc_dev_list);
+    if (c->ooc_ev_table) cudaEventDestroy(c->ooc_ev_table);
+    if (c->ooc_ev_render) cudaEventDestroy(c->ooc_ev_render);
+    if (c->ooc_side) cudaStreamDestroy(c->ooc_side);
+    c->ooc_pin_table = nullptr;
+    c->ooc_pin_list = nullptr;
+    c->ooc_dev_list = nullptr;
+    c->ooc_ev_table = c->ooc_ev_render = nullptr;
+    c->ooc_side = nullptr;
+    c->slot_brick.clear();
+    c->table_host.clear();
+    c->slot_use.clear();
+    c->ooc = false;
+}
+
 void free_cube(vr_ctx* c) {
+    free_ooc(c);
     if (c->pool) cudaFree(c->pool);
     if (c->table) cudaFree(c->table);
     if (c->minmax) cudaFree(c->minmax);
@@ -162,7 +211,7 @@ bool make_tensor_map(vr_ctx* c) {
     if (!enc) return false;
     const cuuint64_t e = c->elem;
     cuuint64_t dims[4] = {(cuuint64_t)c->pitch, (cuuint64_t)c->rows, (cuuint64_t)c->rows,
-                          (cuuint64_t)c->nbx * c->nby * c->nbz};
+                          (cuuint64_t)c->pool_slots};
     cuuint64_t strides[3] = {c->pitch * e, (cuuint64_t)c->rows * c->pitch * e, (cuuint64_t)c->slot_elems * e};
     cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
@@ -343,6 +392,7 @@ vr_status vr_load_cube(vr_ctx* ctx, const float* src, int src_on_device, int64_t
     const long long nbricks = (long long)ctx->nbx * ctx->nby * ctx->nbz;
     if (nbricks > (1LL << 30)) return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube: too many bricks");
     const size_t pool_bytes = (size_t)nbricks * (size_t)ctx->slot_elems * ctx->elem;
+    ctx->pool_slots = nbricks;
     VR_CK(cudaMalloc(&ctx->pool, pool_bytes), "vr_load_cube: brick store allocation");
     VR_CK(cudaMalloc(&ctx->table, sizeof(int) * nbricks), "vr_load_cube: brick table allocation");
     VR_CK(cudaMalloc(&ctx->minmax, sizeof(unsigned int) * 2 * nbricks), "vr_load_cube: range allocation");
@@ -388,6 +438,95 @@ vr_status vr_load_cube(vr_ctx* ctx, const float* src, int src_on_device, int64_t
         VR_CK(cudaMalloc(&ctx->cells, brick_cells_bytes(units)), "vr_load_cube: cell list allocation");
     }
     ctx->has_cube = true;
+    return VR_OK;
+}
+
+vr_status vr_load_cube_streamed(vr_ctx* ctx, vr_region_fn fn, void* user, int64_t nx, int64_t ny, int64_t nz,
+                                vr_dtype storage, uint64_t cache_bytes) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!fn) return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube_streamed: fn is NULL");
+    if (nx <= 0 || ny <= 0 || nz <= 0 || nx >= (1LL << 30) || ny >= (1LL << 30) || nz >= (1LL << 30))
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube_streamed: dimensions must be in [1, 2^30)");
+    if (storage != VR_F32 && storage != VR_F16 && storage != VR_BF16)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube_streamed: unknown storage type");
+    DevGuard g(ctx->device);
+    VR_CK(cudaGetLastError(), "vr_load_cube_streamed: pending CUDA error");
+    VR_CK(cudaDeviceSynchronize(), "vr_load_cube_streamed: drain");
+    free_cube(ctx);
+    const int B = ctx->opt.brick;
+    ctx->B = B;
+    ctx->log2B = ilog2(B);
+    ctx->nx = nx;
+    ctx->ny = ny;
+    ctx->nz = nz;
+    ctx->nbx = (int)((nx + B - 1) / B);
+    ctx->nby = (int)((ny + B - 1) / B);
+    ctx->nbz = (int)((nz + B - 1) / B);
+    ctx->dtype = storage;
+    ctx->elem = storage == VR_F32 ? 4 : 2;
+    ctx->rows = B + 2;
+    const int vec = (int)(16 / ctx->elem);
+    ctx->pitch = (ctx->rows + vec - 1) / vec * vec;
+    const long long se = (long long)ctx->rows * ctx->rows * ctx->pitch;
+    const long long align = 256 / (long long)ctx->elem;
+    ctx->slot_elems = (se + align - 1) / align * align;
+    const long long nbricks = (long long)ctx->nbx * ctx->nby * ctx->nbz;
+    if (nbricks > (1LL << 30)) return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube_streamed: too many bricks");
+    const long long slot_bytes = ctx->slot_elems * (long long)ctx->elem;
+    const long long nslots = std::min<long long>(nbricks, (long long)(cache_bytes / (uint64_t)slot_bytes));
+    if (nslots < 1) return fail(ctx, VR_ERR_INVALID_ARG, "vr_load_cube_streamed: cache smaller than one brick");
+    ctx->pool_slots = nslots;
+    VR_CK(cudaMalloc(&ctx->pool, (size_t)nslots * (size_t)slot_bytes), "vr_load_cube_streamed: brick cache");
+    VR_CK(cudaMalloc(&ctx->table, sizeof(int) * (size_t)nbricks), "vr_load_cube_streamed: brick table");
+    VR_CK(cudaMemset(ctx->table, 0xff, sizeof(int) * (size_t)nbricks), "vr_load_cube_streamed: brick table");
+    ctx->slot_brick.assign((size_t)nslots, -1);
+    ctx->slot_use.assign((size_t)nslots, 0);
+    ctx->table_host.assign((size_t)nbricks, -1);
+    ctx->ooc_tick = 0;
+    ctx->ooc_stats = vr_stream_stats{};
+    const size_t region = sizeof(float) * (size_t)ctx->rows * ctx->rows * ctx->rows;
+    VR_CK(cudaStreamCreateWithFlags(&ctx->ooc_side, cudaStreamNonBlocking), "vr_load_cube_streamed: side stream");
+    for (int i = 0; i < 2; ++i) {
+        VR_CK(cudaHostAlloc(&ctx->ooc_pin[i], region, cudaHostAllocDefault), "vr_load_cube_streamed: staging");
+        VR_CK(cudaMalloc(&ctx->ooc_dev[i], region), "vr_load_cube_streamed: staging");
+        VR_CK(cudaEventCreateWithFlags(&ctx->ooc_ev[i], cudaEventDisableTiming), "vr_load_cube_streamed: events");
+        VR_CK(cudaEventRecord(ctx->ooc_ev[i], ctx->ooc_side), "vr_load_cube_streamed: events");
+    }
+    VR_CK(cudaEventCreateWithFlags(&ctx->ooc_ev_table, cudaEventDisableTiming), "vr_load_cube_streamed: events");
+    VR_CK(cudaEventRecord(ctx->ooc_ev_table, ctx->ooc_side), "vr_load_cube_streamed: events");
+    VR_CK(cudaEventCreateWithFlags(&ctx->ooc_ev_render, cudaEventDisableTiming), "vr_load_cube_streamed: events");
+    VR_CK(cudaHostAlloc(&ctx->ooc_pin_table, sizeof(int) * (size_t)nbricks, cudaHostAllocDefault),
+          "vr_load_cube_streamed: table staging");
+    VR_CK(cudaHostAlloc(&ctx->ooc_pin_list, sizeof(int) * (size_t)(2 * (nslots + 1)), cudaHostAllocDefault),
+          "vr_load_cube_streamed: list staging");
+    VR_CK(cudaMalloc(&ctx->ooc_dev_list, sizeof(int) * (size_t)(3 * (nslots + 1))), "vr_load_cube_streamed: lists");
+    ctx->ooc_fn = fn;
+    ctx->ooc_user = user;
+    ctx->ooc = true;
+    if (make_tensor_map(ctx)) {
+        int cx, cy, cz;
+        brick_cell_dims(ctx->dtype, &cx, &cy, &cz);
+        const long long units = nslots * (long long)(B / cx) * (B / cy) * (B / cz);
+        VR_CK(cudaMalloc(&ctx->cells, brick_cells_bytes(units)), "vr_load_cube_streamed: cell list");
+    } else {
+        free_cube(ctx);
+        return fail(ctx, VR_ERR_UNSUPPORTED, "vr_load_cube_streamed: needs bricks of at least 32 voxels");
+    }
+    VR_CK(cudaStreamSynchronize(ctx->ooc_side), "vr_load_cube_streamed: set-up");
+    ctx->has_cube = true;
+    return VR_OK;
+}
+
+vr_status vr_get_stream_stats(const vr_ctx* ctx, vr_stream_stats* out) {
+    if (!ctx || !out) return VR_ERR_INVALID_ARG;
+    if (!ctx->ooc) return VR_ERR_STATE;
+    *out = ctx->ooc_stats;
+    return VR_OK;
+}
+
+vr_status vr_set_stream_timeout(vr_ctx* ctx, double seconds) {
+    if (!ctx || !(seconds > 0.0) || !std::isfinite(seconds)) return VR_ERR_INVALID_ARG;
+    ctx->ooc_timeout_s = seconds;
     return VR_OK;
 }
 
@@ -754,6 +893,290 @@ vr_status render_bricks_composite(vr_ctx* ctx, float* out_rgba, cudaStream_t s, 
     return VR_OK;
 }
 
+// ------------------------------------------------------------------ out of core
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Host wait for a device event, bounded by the context's deadline.
+vr_status wait_event(vr_ctx* ctx, cudaEvent_t e, const char* what) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t q = cudaEventQuery(e);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_fail(ctx, q, what);
+        if (seconds_since(t0) > ctx->ooc_timeout_s) {
+            ctx->ooc_stats.wait_s += seconds_since(t0);
+            return fail(ctx, VR_ERR_TIMEOUT, std::string(what) + ": device wait exceeded the deadline");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    ctx->ooc_stats.wait_s += seconds_since(t0);
+    return VR_OK;
+}
+
+// Make the bricks of `list` resident (render stream s waits for them).  Slots
+// in use by this batch are never evicted; the batch must fit the cache.
+vr_status ensure_resident(vr_ctx* ctx, const int* list, int n, cudaStream_t s) {
+    const long long tick = ++ctx->ooc_tick;
+    const int nslots = (int)ctx->pool_slots;
+    if (n > nslots) return fail(ctx, VR_ERR_INTERNAL, "out-of-core batch larger than the brick cache");
+    for (int i = 0; i < n; ++i) {
+        const int sl = ctx->table_host[(size_t)list[i]];
+        if (sl >= 0) ctx->slot_use[(size_t)sl] = tick;
+    }
+    // the side stream must not overwrite a slot that earlier render work still reads
+    VR_CK(cudaEventRecord(ctx->ooc_ev_render, s), "out of core: render event");
+    VR_CK(cudaStreamWaitEvent(ctx->ooc_side, ctx->ooc_ev_render, 0), "out of core: stream order");
+    const int B = ctx->B;
+    const VolDev v = vol_dev(ctx);
+    bool changed = false;
+    for (int i = 0; i < n; ++i) {
+        const int b = list[i];
+        if (ctx->table_host[(size_t)b] >= 0) continue;
+        // a free slot, else the least recently used one not needed by this batch
+        int slot = -1;
+        long long best = tick;
+        for (int sl = 0; sl < nslots; ++sl) {
+            if (ctx->slot_brick[(size_t)sl] < 0) {
+                slot = sl;
+                break;
+            }
+            if (ctx->slot_use[(size_t)sl] < best) {
+                best = ctx->slot_use[(size_t)sl];
+                slot = sl;
+            }
+        }
+        if (slot < 0) return fail(ctx, VR_ERR_INTERNAL, "out of core: no evictable slot");
+        if (ctx->slot_brick[(size_t)slot] >= 0) ctx->table_host[(size_t)ctx->slot_brick[(size_t)slot]] = -1;
+        ctx->slot_brick[(size_t)slot] = -1;
+        const int bx = b % ctx->nbx, by = (b / ctx->nbx) % ctx->nby, bz = b / (ctx->nbx * ctx->nby);
+        const long long x0 = std::max<long long>((long long)bx * B - 1, 0), x1 = std::min<long long>((long long)bx * B + B + 1, ctx->nx);
+        const long long y0 = std::max<long long>((long long)by * B - 1, 0), y1 = std::min<long long>((long long)by * B + B + 1, ctx->ny);
+        const long long z0 = std::max<long long>((long long)bz * B - 1, 0), z1 = std::min<long long>((long long)bz * B + B + 1, ctx->nz);
+        const int buf = ctx->ooc_next_buf;
+        ctx->ooc_next_buf ^= 1;
+        vr_status st = wait_event(ctx, ctx->ooc_ev[buf], "out of core: staging buffer");  // its last upload
+        if (st != VR_OK) return st;
+        const auto t0 = std::chrono::steady_clock::now();
+        const int rc = ctx->ooc_fn(ctx->ooc_user, x0, y0, z0, x1 - x0, y1 - y0, z1 - z0, ctx->ooc_pin[buf]);
+        const double dt = seconds_since(t0);
+        ctx->ooc_stats.generate_s += dt;
+        if (rc != 0) return fail(ctx, VR_ERR_IO, "out of core: the region callback failed (" + std::to_string(rc) + ")");
+        if (dt > ctx->ooc_timeout_s) return fail(ctx, VR_ERR_TIMEOUT, "out of core: the region callback exceeded the deadline");
+        const size_t bytes = sizeof(float) * (size_t)((x1 - x0) * (y1 - y0) * (z1 - z0));
+        VR_CK(cudaMemcpyAsync(ctx->ooc_dev[buf], ctx->ooc_pin[buf], bytes, cudaMemcpyHostToDevice, ctx->ooc_side),
+              "out of core: upload");
+        void* slotp = static_cast<char*>(ctx->pool) + (size_t)slot * ctx->slot_elems * ctx->elem;
+        VR_CK(launch_repack_region(ctx->ooc_dev[buf], (int)x0, (int)y0, (int)z0, (int)(x1 - x0), (int)(y1 - y0),
+                                   (int)(z1 - z0), bx, by, bz, v, ctx->dtype, slotp, ctx->ooc_side),
+              "out of core: repack");
+        VR_CK(cudaEventRecord(ctx->ooc_ev[buf], ctx->ooc_side), "out of core: upload event");
+        ctx->slot_brick[(size_t)slot] = b;
+        ctx->table_host[(size_t)b] = slot;
+        ctx->slot_use[(size_t)slot] = tick;
+        ctx->ooc_stats.bricks_fetched++;
+        ctx->ooc_stats.bytes_h2d += bytes;
+        changed = true;
+    }
+    if (changed) {
+        // publish the brick table (the previous upload of the staging copy must be done)
+        vr_status st = wait_event(ctx, ctx->ooc_ev_table, "out of core: table upload");
+        if (st != VR_OK) return st;
+        const size_t nb = (size_t)ctx->nbx * ctx->nby * ctx->nbz;
+        std::memcpy(ctx->ooc_pin_table, ctx->table_host.data(), sizeof(int) * nb);
+        VR_CK(cudaMemcpyAsync(ctx->table, ctx->ooc_pin_table, sizeof(int) * nb, cudaMemcpyHostToDevice, ctx->ooc_side),
+              "out of core: table upload");
+        VR_CK(cudaEventRecord(ctx->ooc_ev_table, ctx->ooc_side), "out of core: table event");
+    }
+    VR_CK(cudaEventRecord(ctx->ooc_ev_render, ctx->ooc_side), "out of core: ready event");
+    VR_CK(cudaStreamWaitEvent(s, ctx->ooc_ev_render, 0), "out of core: stream order");
+    ctx->ooc_stats.batches++;
+    return VR_OK;
+}
+
+// Footprints and visibility order of one camera (read back to the host).
+vr_status ooc_footprints(vr_ctx* ctx, const CamDev& cd, SortParams& sp, std::vector<int>& order,
+                         std::vector<int>& layer_start, std::vector<BrickFoot>& foot, cudaStream_t s) {
+    const long long nbricks = (long long)ctx->nbx * ctx->nby * ctx->nbz;
+    if (nbricks + 1 > ctx->sort_bricks) {
+        if (ctx->foot) cudaFree(ctx->foot);
+        if (ctx->order) cudaFree(ctx->order);
+        if (ctx->tile_start) cudaFree(ctx->tile_start);
+        ctx->foot = nullptr;
+        ctx->order = nullptr;
+        ctx->tile_start = nullptr;
+        ctx->sort_bricks = 0;
+        VR_CK(cudaMalloc(&ctx->foot, sizeof(BrickFoot) * (size_t)nbricks), "out of core: scratch");
+        VR_CK(cudaMalloc(&ctx->order, sizeof(int) * (size_t)nbricks), "out of core: scratch");
+        VR_CK(cudaMalloc(&ctx->tile_start, sizeof(int) * (size_t)(nbricks + 1)), "out of core: scratch");
+        ctx->sort_bricks = nbricks + 1;
+    }
+    if (!ctx->partial_used) VR_CK(cudaMalloc(&ctx->partial_used, sizeof(unsigned long long)), "out of core: scratch");
+    const int L = layer_bound(ctx, cd);
+    if (L + 1 > ctx->layer_cap) {
+        if (ctx->layer_buf) cudaFree(ctx->layer_buf);
+        ctx->layer_buf = nullptr;
+        ctx->layer_cap = 0;
+        VR_CK(cudaMalloc(&ctx->layer_buf, sizeof(int) * 3 * (size_t)(L + 1)), "out of core: scratch");
+        ctx->layer_cap = L + 1;
+    }
+    if (!cam_ff(cd, sp.cam)) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: camera basis is singular");
+    for (int ax = 0; ax < 3; ++ax)
+        sp.eye_brick[ax] = (int)std::max<double>(-(1 << 20), std::min<double>(1 << 20, std::floor(cd.eye[ax] / (double)ctx->B)));
+    sp.all_bricks = 1;
+    sp.max_layers = L;
+    sp.foot = ctx->foot;
+    sp.order = ctx->order;
+    sp.tile_start = ctx->tile_start;
+    sp.partial_used = ctx->partial_used;
+    sp.layer_count = ctx->layer_buf;
+    sp.layer_start = ctx->layer_buf + (L + 1);
+    sp.layer_fill = ctx->layer_buf + 2 * (L + 1);
+    VR_CK(cudaMemsetAsync(sp.layer_count, 0, sizeof(int) * (size_t)L, s), "out of core: reset");
+    VR_CK(cudaMemsetAsync(sp.partial_used, 0, sizeof(unsigned long long), s), "out of core: reset");
+    VR_CK(launch_brick_footprints(sp, s), "out of core: footprints");
+    layer_start.resize((size_t)L + 1);
+    VR_CK(cudaMemcpyAsync(layer_start.data(), sp.layer_start, sizeof(int) * (size_t)(L + 1), cudaMemcpyDeviceToHost, s),
+          "out of core: read-back");
+    VR_CK(cudaStreamSynchronize(s), "out of core: read-back");
+    const int nvis = layer_start[(size_t)L];
+    order.resize((size_t)nvis);
+    foot.resize((size_t)nbricks);
+    if (nvis > 0) {
+        VR_CK(cudaMemcpy(order.data(), sp.order, sizeof(int) * (size_t)nvis, cudaMemcpyDeviceToHost), "out of core: read-back");
+        VR_CK(cudaMemcpy(foot.data(), sp.foot, sizeof(BrickFoot) * (size_t)nbricks, cudaMemcpyDeviceToHost),
+              "out of core: read-back");
+    }
+    return VR_OK;
+}
+
+vr_status render_ooc(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, cudaStream_t s) {
+    const int W = ctx->cams[0].width, H = ctx->cams[0].height;
+    const long long img = (long long)W * H;
+    vr_status st = ensure_pixel_scratch(ctx, img);
+    if (st != VR_OK) return st;
+    if (mode == VR_COMPOSITE) {
+        st = grow(ctx, ctx->state, ctx->state_cap, img, "layered state");
+        if (st != VR_OK) return st;
+    }
+    const int nslots = (int)ctx->pool_slots;
+    SortParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.vol = vol_dev(ctx);
+    sp.tf = tf_dev(ctx);
+    sp.step = (float)ctx->opt.step;
+    sp.ert = (float)ctx->opt.ert;
+    sp.krange = ctx->krange;
+    sp.state = ctx->state;
+    PixelParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.vol = sp.vol;
+    pp.tf = sp.tf;
+    pp.step = ctx->opt.step;
+    pp.width = W;
+    pp.height = H;
+    pp.krange = ctx->krange;
+    BrickParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.vol = sp.vol;
+    bp.step = (float)ctx->opt.step;
+    bp.width = W;
+    bp.height = H;
+    bp.ncams = 1;
+    int cx, cy, cz;
+    brick_cell_dims(ctx->dtype, &cx, &cy, &cz);
+    bp.ncells_x = ctx->B / cx;
+    bp.ncells_y = ctx->B / cy;
+    bp.ncells_z = ctx->B / cz;
+    bp.nbricks = ctx->nbx * ctx->nby * ctx->nbz;
+    bp.krange = ctx->krange;
+    bp.status = ctx->status_dev;
+    std::vector<int> order, layer_start, list;
+    std::vector<BrickFoot> foot;
+    for (size_t ci = 0; ci < ctx->cams.size(); ++ci) {
+        const CamDev& cd = ctx->cams[ci];
+        st = ooc_footprints(ctx, cd, sp, order, layer_start, foot, s);
+        if (st != VR_OK) return st;
+        pp.cam = cd;
+        pp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)ci * img;
+        pp.out_max = out_max ? out_max + (long long)ci * img : nullptr;
+        pp.enc = (mode == VR_MIP && out_max) ? reinterpret_cast<unsigned int*>(pp.out_max) : ctx->enc;
+        VR_CK(launch_pixel_setup(pp, s), "out of core: pixel set-up");
+        if (mode == VR_MIP) {
+            if (!cam_ff(cd, bp.cams[0])) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: camera basis is singular");
+            bp.out_enc = pp.enc;
+            // batches of visible bricks in visibility order, as many as the cache holds
+            for (size_t b0 = 0; b0 < order.size(); b0 += (size_t)nslots) {
+                const int n = (int)std::min<size_t>((size_t)nslots, order.size() - b0);
+                st = ensure_resident(ctx, order.data() + b0, n, s);
+                if (st != VR_OK) return st;
+                bp.brick_list = sp.order + b0;  // the same list, still on the device
+                bp.nlist = n;
+                bp.work = ctx->work;
+                VR_CK(cudaMemsetAsync(bp.work, 0, sizeof(int), s), "out of core: scheduler reset");
+                VR_CK(launch_brick_mip(&ctx->tmap, bp, ctx->dtype, 2 * ctx->num_sms, ctx->cells, s, ctx->tune.group),
+                      "out of core: brick pass");
+            }
+            VR_CK(launch_mip_finalize(pp, s), "out of core: finalise");
+            continue;
+        }
+        // composite: layer by layer, skipping bricks behind terminated pixels
+        sp.out_rgba = pp.out_rgba;
+        VR_CK(launch_state_init(sp, s), "out of core: state init");
+        const int L = sp.max_layers;
+        for (int l = 0; l < L; ++l) {
+            const int l0 = layer_start[(size_t)l], l1 = layer_start[(size_t)l + 1];
+            if (l1 == l0) continue;
+            const int n = l1 - l0;
+            int* flags = ctx->ooc_dev_list + 2 * (nslots + 1);  // scratch after the two lists
+            // flags for this layer's bricks, computed in chunks of up to nslots
+            list.clear();
+            for (int c0 = 0; c0 < n; c0 += nslots) {
+                const int m = std::min(nslots, n - c0);
+                VR_CK(launch_bricks_open(sp.foot, sp.order + l0 + c0, m, ctx->state, W, sp.ert, flags, s),
+                      "out of core: open test");
+                VR_CK(cudaMemcpyAsync(ctx->ooc_pin_list, flags, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost, s),
+                      "out of core: read-back");
+                VR_CK(cudaStreamSynchronize(s), "out of core: read-back");
+                for (int i = 0; i < m; ++i) {
+                    if (ctx->ooc_pin_list[i]) list.push_back(order[(size_t)(l0 + c0 + i)]);
+                    else ctx->ooc_stats.bricks_culled++;
+                }
+            }
+            for (size_t b0 = 0; b0 < list.size(); b0 += (size_t)nslots) {
+                const int m = (int)std::min<size_t>((size_t)nslots, list.size() - b0);
+                st = ensure_resident(ctx, list.data() + b0, m, s);
+                if (st != VR_OK) return st;
+                // the batch and its 8 x 4 tile prefix, to the device
+                int* pin = ctx->ooc_pin_list;
+                int acc = 0;
+                for (int i = 0; i < m; ++i) {
+                    const int4 r = foot[(size_t)list[b0 + (size_t)i]].rect;
+                    pin[i] = list[b0 + (size_t)i];
+                    pin[nslots + 1 + i] = acc;
+                    acc += ((r.z - r.x + 1 + 7) / 8) * ((r.w - r.y + 1 + 3) / 4);
+                }
+                pin[nslots + 1 + m] = acc;
+                VR_CK(cudaMemcpyAsync(ctx->ooc_dev_list, pin, sizeof(int) * (size_t)(2 * (nslots + 1)),
+                                      cudaMemcpyHostToDevice, s),
+                      "out of core: batch upload");
+                sp.sub_order = ctx->ooc_dev_list;
+                sp.sub_tile = ctx->ooc_dev_list + nslots + 1;
+                sp.sub_n = m;
+                sp.work = ctx->work;
+                VR_CK(cudaMemsetAsync(sp.work, 0, sizeof(int), s), "out of core: scheduler reset");
+                VR_CK(launch_brick_partial(sp, ctx->dtype, true, 0, 0, ctx->num_sms * 8, s), "out of core: layer");
+                // the pinned batch buffer is reused by the next batch: wait for this upload
+                VR_CK(cudaStreamSynchronize(s), "out of core: batch");
+            }
+        }
+        sp.sub_order = nullptr;
+        VR_CK(launch_state_finish(sp, s), "out of core: state finish");
+    }
+    return VR_OK;
+}
+
 }  // namespace
 
 namespace vr {
@@ -772,6 +1195,7 @@ vr_status brick_mip_precheck(vr_ctx* ctx, float* out_rgba, float* out_max, int* 
     if (ctx->cams.empty()) return fail(ctx, VR_ERR_STATE, "no camera set");
     if (!ctx->has_tmap)
         return fail(ctx, VR_ERR_UNSUPPORTED, "the brick pass needs bricks of at least 32 voxels");
+    if (ctx->ooc) return fail(ctx, VR_ERR_UNSUPPORTED, "not for out-of-core cubes");
     if (*ctx->status_host != 0) {
         const int code = *ctx->status_host;
         *ctx->status_host = 0;
@@ -860,6 +1284,7 @@ vr_path resolve_path(const vr_ctx* ctx, vr_mode mode) {
 
 // The launches of one render on stream s (no allocation: scratch is sized first).
 vr_status render_dispatch(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, cudaStream_t s) {
+    if (ctx->ooc) return render_ooc(ctx, mode, out_rgba, out_max, s);
     vr_path path = resolve_path(ctx, mode);
     if ((path == VR_PATH_SORTLAST || path == VR_PATH_LAYERED) && mode == VR_COMPOSITE)
         return render_bricks_composite(ctx, out_rgba, s, path == VR_PATH_LAYERED);
@@ -958,7 +1383,8 @@ vr_status vr_render(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VR_CK(cudaGetLastError(), "vr_render: pending CUDA error");
     const vr_path path = resolve_path(ctx, mode);
-    const bool host_steered = (path == VR_PATH_SORTLAST || path == VR_PATH_LAYERED) && mode == VR_COMPOSITE;
+    const bool host_steered = ((path == VR_PATH_SORTLAST || path == VR_PATH_LAYERED) && mode == VR_COMPOSITE) ||
+                              ctx->ooc;
     if (ctx->graph_mode && !host_steered) return render_graphed(ctx, mode, out_rgba, out_max, s);
     return render_dispatch(ctx, mode, out_rgba, out_max, s);
 }
@@ -990,6 +1416,7 @@ vr_status vr_autotune(vr_ctx* ctx, vr_mode mode, float* scratch_rgba, int reps, 
     if (reps < 1 || reps > 1000) return fail(ctx, VR_ERR_INVALID_ARG, "vr_autotune: reps in [1, 1000]");
     vr_status st = render_checks(ctx, mode, scratch_rgba, nullptr);
     if (st != VR_OK) return st;
+    if (ctx->ooc) return fail(ctx, VR_ERR_UNSUPPORTED, "vr_autotune: not for out-of-core cubes");
     DevGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<vr_tuning> cands;
@@ -1048,6 +1475,7 @@ vr_status vr_render_backward(vr_ctx* ctx, vr_mode mode, const float* dL_dimg, fl
         reinterpret_cast<uintptr_t>(dL_dvol) % 4)
         return fail(ctx, VR_ERR_INVALID_ARG, "vr_render_backward: dL_dimg must be 16-byte aligned");
     if (!ctx->has_cube) return fail(ctx, VR_ERR_STATE, "vr_render_backward: no cube loaded");
+    if (ctx->ooc) return fail(ctx, VR_ERR_UNSUPPORTED, "vr_render_backward: not for out-of-core cubes");
     if (!ctx->has_tf) return fail(ctx, VR_ERR_STATE, "vr_render_backward: no transfer function set");
     if (ctx->cams.empty()) return fail(ctx, VR_ERR_STATE, "vr_render_backward: no camera set");
     if (*ctx->status_host != 0) {

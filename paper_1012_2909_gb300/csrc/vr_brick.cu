@@ -288,13 +288,16 @@ struct CellDesc {
 template <typename T>
 __global__ void k_cell_list(const __grid_constant__ BrickParams P, CellDesc* __restrict__ list,
                             int* __restrict__ count) {
-    const int nunits = P.nbricks * P.ncells_x * P.ncells_y * P.ncells_z;
+    // units: every cell of every brick, or of the bricks of an explicit list
+    const int ncells = P.ncells_x * P.ncells_y * P.ncells_z;
+    const int nunits = (P.brick_list ? P.nlist : P.nbricks) * ncells;
     const int lane = threadIdx.x & 31;
     for (int u0 = blockIdx.x * blockDim.x; u0 < nunits; u0 += gridDim.x * blockDim.x) {
-        const int u = u0 + threadIdx.x;
+        int u = u0 + threadIdx.x;
+        if (P.brick_list && u < nunits) u = P.brick_list[u / ncells] * ncells + u % ncells;
         float3 lo;
         int4 coord;
-        bool ok = u < nunits && unit_cell<T>(P, u, lo, coord);
+        bool ok = u0 + threadIdx.x < nunits && unit_cell<T>(P, u, lo, coord);
         int4 rect0 = make_int4(0, 0, -1, -1);
         if (ok) {
             bool any = cam_cell_rect<T>(P.cams[0], lo, rect0);
@@ -563,7 +566,7 @@ template <typename T>
 cudaError_t launch_t(const void* tmap, const BrickParams& p, int grid, void* cells, cudaStream_t s, int group) {
     CellDesc* list = reinterpret_cast<CellDesc*>(static_cast<char*>(cells) + 256);
     int* count = static_cast<int*>(cells);
-    const int nunits = p.nbricks * p.ncells_x * p.ncells_y * p.ncells_z;
+    const int nunits = (p.brick_list ? p.nlist : p.nbricks) * p.ncells_x * p.ncells_y * p.ncells_z;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     k_cell_list<T><<<std::min((nunits + 255) / 256, 4096), 256, 0, s>>>(p, list, count);

@@ -85,6 +85,8 @@ struct BrickParams {
     int nbricks;
     const int2* krange;      // per pixel [k0, k1) from the double-precision set-up
     unsigned int* out_enc;   // per pixel ordered-int encoding of the running maximum
+    const int* brick_list;   // optional: only the cells of these bricks (out-of-core batches)
+    int nlist, pad_l;
     int* work;               // brick counter (zeroed)
     int* status;             // device status word (0 = ok)
 };
@@ -122,7 +124,7 @@ struct SortParams {
     CamFF cam;
     float step, ert;
     int max_layers, pad;
-    int eye_brick[3], pad2;           // floor(eye / B) (perspective visibility keys)
+    int eye_brick[3], all_bricks;     // floor(eye / B); all_bricks: ignore residency (out of core)
     const int2* krange;
     BrickFoot* foot;                  // per brick
     int* order;                       // visible bricks grouped by layer
@@ -135,6 +137,9 @@ struct SortParams {
     float4* state;                    // running (C, T) per pixel (layered path)
     float4* out_rgba;
     int* work;                        // zeroed work counter of a launch
+    const int* sub_order;             // optional explicit brick subset (out-of-core batches)
+    const int* sub_tile;              // its tile prefix (sub_n + 1)
+    int sub_n, pad3;
 };
 
 // Per-pixel set-up and finalisation around the brick pass.
@@ -175,6 +180,10 @@ cudaError_t launch_brick_partial(const SortParams& p, vr_dtype dt, bool carried,
 cudaError_t launch_sortlast_fold(const SortParams& p, cudaStream_t s);
 cudaError_t launch_state_init(const SortParams& p, cudaStream_t s);
 cudaError_t launch_state_finish(const SortParams& p, cudaStream_t s);
+cudaError_t launch_repack_region(const float* src, int rx0, int ry0, int rz0, int rsx, int rsy, int rsz, int bx,
+                                 int by, int bz, const VolDev& v, vr_dtype dt, void* slot, cudaStream_t s);
+cudaError_t launch_bricks_open(const BrickFoot* foot, const int* list, int n, const float4* state, int width,
+                               float ert, int* flags, cudaStream_t s);
 int adjoint_threads();
 int adjoint_blocks_per_sm(vr_dtype dt, int mode, int ntf);
 cudaError_t launch_adjoint(const AdjParams& p, vr_dtype dt, int grid, cudaStream_t s);

@@ -89,7 +89,7 @@ __global__ void k_brick_footprints(const __grid_constant__ SortParams P) {
         const float3 hi = make_float3((float)min((bx + 1) * B, P.vol.nx), (float)min((by + 1) * B, P.vol.ny),
                                       (float)min((bz + 1) * B, P.vol.nz));
         int4 r = make_int4(0, 0, -1, -1);
-        const bool vis = P.vol.table[b] >= 0 && box_rect(c, lo, hi, r);
+        const bool vis = (P.all_bricks || P.vol.table[b] >= 0) && box_rect(c, lo, hi, r);
         int key;
         if (c.type == 1) {
             key = abs(bx - ex) + abs(by - ey) + abs(bz - ez);
@@ -247,8 +247,12 @@ k_brick_partial(const __grid_constant__ SortParams P, int layer_begin, int layer
     for (int i = threadIdx.x; i < P.tf.n; i += blockDim.x) s_tf[i] = P.tf.tab[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int first = P.layer_start[layer_begin], end = P.layer_start[layer_end];
-    const int t0 = P.tile_start[first], t1 = P.tile_start[end];
+    // the bricks of layers [layer_begin, layer_end) of the ordered list, or an explicit subset
+    const int* order = P.sub_order ? P.sub_order : P.order;
+    const int* tile_start = P.sub_order ? P.sub_tile : P.tile_start;
+    const int first = P.sub_order ? 0 : P.layer_start[layer_begin];
+    const int end = P.sub_order ? P.sub_n : P.layer_start[layer_end];
+    const int t0 = tile_start[first], t1 = tile_start[end];
     const T* __restrict__ pool = static_cast<const T*>(P.vol.pool);
     const float ert = P.ert;
     for (;;) {
@@ -261,13 +265,13 @@ k_brick_partial(const __grid_constant__ SortParams P, int layer_begin, int layer
         int lo = first, hi = end - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (P.tile_start[mid] <= gt) lo = mid; else hi = mid - 1;
+            if (tile_start[mid] <= gt) lo = mid; else hi = mid - 1;
         }
-        const int b = P.order[lo];
+        const int b = order[lo];
         const BrickFoot f = P.foot[b];
         const int4 rect = f.rect;
         const int tx_n = (rect.z - rect.x + 1 + 7) / 8;
-        const int rem = gt - P.tile_start[lo];
+        const int rem = gt - tile_start[lo];
         const int ty = rem / tx_n, tx = rem - ty * tx_n;
         const int px = rect.x + tx * 8 + (lane & 7), py = rect.y + ty * 4 + (lane >> 3);
         if (px > rect.z || py > rect.w) continue;  // ragged tile; the lane rejoins at the shuffle

@@ -66,6 +66,21 @@ def _load():
     return _lib
 
 
+class SynCbUser(ctypes.Structure):
+    _fields_ = [("p", SynParams), ("nthreads", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+def region_callback(p: dict, nthreads: int | None = None):
+    """(C function pointer, user struct) of the generator's region callback, for
+    renderers that pull cube regions on demand (the struct must be kept alive)."""
+    lib = _load()
+    u = SynCbUser()
+    u.p = _params(p)
+    u.nthreads = int(nthreads or os.cpu_count() or 1)
+    fn = ctypes.cast(lib.syn_region_cb, ctypes.c_void_p)
+    return fn, u
+
+
 def lib_handle():
     """The loaded generator library (for callers that want its C entry points)."""
     return _load()

@@ -193,11 +193,25 @@ int syn_region(const syn_params* p, int64_t x0, int64_t y0, int64_t z0,
         return -1;
     if (sx == 0 || sy == 0 || sz == 0) return 0;
     syn_source* src = NULL;
+    syn_params q = *p; /* the same cube with only the sources that reach the region */
     if (p->nsrc > 0) {
         src = (syn_source*)malloc(sizeof(syn_source) * (size_t)p->nsrc);
         if (!src) return -1;
         syn_sources(p, src);
+        int32_t kept = 0;
+        for (int32_t s = 0; s < p->nsrc; ++s) {
+            int64_t a, b;
+            idx_range(src[s].cx, src[s].sig_s, p->trunc, x0, x0 + sx, &a, &b);
+            if (a >= b) continue;
+            idx_range(src[s].cy, src[s].sig_s, p->trunc, y0, y0 + sy, &a, &b);
+            if (a >= b) continue;
+            idx_range(src[s].cz, src[s].sig_z, p->trunc, z0, z0 + sz, &a, &b);
+            if (a >= b) continue;
+            src[kept++] = src[s]; /* order kept: sources are still added in index order */
+        }
+        q.nsrc = kept;
     }
+    p = &q;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > sz) nthreads = (int)sz;
     if (nthreads > 256) nthreads = 256;
@@ -223,4 +237,23 @@ int syn_region(const syn_params* p, int64_t x0, int64_t y0, int64_t z0,
         if (jobs[t].rc) rc = -1;
     free(src);
     return rc;
+}
+
+/*
+ * Region callback for out-of-core renderers: `user` points to a syn_cb_user
+ * (parameters + worker count).  Signature: fill dst with the region
+ * [x0, x0+sx) x [y0, y0+sy) x [z0, z0+sz), x fastest; 0 on success.
+ */
+typedef struct {
+    syn_params p;
+    int32_t nthreads;
+    int32_t pad_;
+} syn_cb_user;
+
+int syn_region_cb(void* user, int64_t x0, int64_t y0, int64_t z0, int64_t sx, int64_t sy, int64_t sz,
+                  float* dst)
+{
+    const syn_cb_user* u = (const syn_cb_user*)user;
+    if (!u) return -1;
+    return syn_region(&u->p, x0, y0, z0, sx, sy, sz, dst, u->nthreads);
 }
