@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--cube", default=None,
                     help="NX,NY,NZ: override the cube size (same source density) for small captures")
     ap.add_argument("--frame", type=int, default=None, help="with --profile: render this frame only")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the wall / gradient / out-of-core measurements")
     return ap.parse_args()
 
 
@@ -151,6 +153,142 @@ def sample_pixels(W, H, n, seed):
     import numpy as np
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(W * H, size=min(n, W * H), replace=False))
+
+
+
+def _events_ms(fn, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_wall(dev):
+    """5 x 5 wall of 1920 x 1080 panels (25 off-axis frusta of one camera) on the
+    2048 x 2048 x 1024 FP16 cube: batched (one graph launch per mode, autotuned)
+    versus the 25 panels rendered one by one."""
+    import torch
+
+    import paper_1012_2909_gb300 as vr
+    import synth
+    cfg = synth.CONFIGS["wall"]
+    p = cfg["cube"]
+    dims = (p["nx"], p["ny"], p["nz"])
+    W, H = cfg["image"]
+    vol = synth.generate(p)
+    r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
+    r.load_cube(vol, "f16")
+    del vol
+    r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
+    big = synth.orbit_view(dims, 30.0, 5 * W, 5 * H)
+    panels = synth.wall_views(big, 5, 5)
+    out = {}
+    counter = torch.zeros(1, dtype=torch.int64, device=f"cuda:{dev}")
+    r.set_camera(panels)
+    r.set_path("ray")
+    vr.vr_set_sample_counter(r.ctx, counter)
+    for mode in ("composite", "mip"):
+        counter.zero_()
+        r.render(mode)
+        torch.cuda.synchronize()
+        out[f"{mode}_samples"] = int(counter.item())
+    vr.vr_set_sample_counter(r.ctx, None)
+    r.set_path("auto")
+    tune = {m: vr.autotune(r, m, reps=2) for m in ("composite", "mip")}
+    img = torch.empty((25, H, W, 4), device=f"cuda:{dev}")
+    vr.vr_set_graph(r.ctx, True)
+    for mode in ("composite", "mip"):
+        out[f"{mode}_batched_ms"] = _events_ms(lambda: r.render(mode, out=img), 3)
+    vr.vr_set_graph(r.ctx, False)
+    one = torch.empty((1, H, W, 4), device=f"cuda:{dev}")
+    for mode in ("composite", "mip"):
+        def singles():
+            for c in panels:
+                r.set_camera(c)
+                r.render(mode, out=one)
+        out[f"{mode}_25_single_ms"] = _events_ms(singles, 1)
+        r.set_camera(panels)
+    for mode in ("composite", "mip"):
+        out[f"{mode}_samples_per_s"] = out[f"{mode}_samples"] / (out[f"{mode}_batched_ms"] / 1e3)
+        out[f"{mode}_batching_speedup"] = out[f"{mode}_25_single_ms"] / out[f"{mode}_batched_ms"]
+    out["tuning"] = {m: {k: v for k, v in t.items() if k != "cached"} for m, t in tune.items()}
+    out["workload"] = "2048x2048x1024 FP16, 25 x 1920x1080 off-axis frusta (9600x5400), graph mode"
+    r.close()
+    return out
+
+
+def extra_diff(dev):
+    """Gradient workload: 256^3 FP32 (noise + 50 sources), 64 seeded views at 512^2,
+    L2 loss against images of a hidden table; forward + adjoint per step."""
+    import torch
+
+    import paper_1012_2909_gb300 as vr
+    import synth
+    cfg = synth.CONFIGS["diff"]
+    p = cfg["cube"]
+    dims = (p["nx"], p["ny"], p["nz"])
+    vol = synth.generate(p)
+    views = synth.random_views(dims, cfg["views"], seed=cfg["view_seed"], width=512, height=512)
+    r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
+    r.load_cube(vol, "f32")
+    r.set_camera(views)
+    r.set_transfer_function(synth.hidden_tf(cfg["tf_seed"]), -1.0, 20.0)
+    target = r.render("composite").clone()
+    r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
+    dtf = torch.empty((256, 4), device=f"cuda:{dev}")
+    dvol = torch.empty(vol.shape, device=f"cuda:{dev}")
+    img = torch.empty_like(target)
+
+    def step():
+        r.render("composite", out=img)
+        dimg = 2.0 * (img - target) / img.numel()
+        vr.vr_render_backward(r.ctx, "composite", dimg, dtf, dvol)
+
+    step()
+    fwd = _events_ms(lambda: r.render("composite", out=img), 3)
+    both = _events_ms(step, 3)
+    r.close()
+    return {"workload": "256^3 FP32, 64 views 512x512, L2 loss, forward + adjoint (table + voxels)",
+            "forward_ms": fwd, "step_ms": both, "backward_ms": both - fwd}
+
+
+def extra_ooc(dev, cache_gib=32):
+    """Out-of-core: 4096 x 4096 x 8192 FP16 cube (256 GiB) produced brick by brick from
+    the generator, 32 GiB HBM cache; one composite frame of the orbit (front bricks
+    only: rays terminate early, bricks behind them are never fetched)."""
+    import torch
+
+    import paper_1012_2909_gb300 as vr
+    import synth
+    cfg = synth.CONFIGS["ooc"]
+    p = cfg["cube"]
+    dims = (p["nx"], p["ny"], p["nz"])
+    r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
+    fn, user = synth.region_callback(p)
+    vr.vr_load_cube_streamed(r.ctx, fn, user, dims, "f16", cache_bytes=cache_gib << 30)
+    r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
+    r.set_camera(synth.orbit_view(dims, 0.0))
+    t0 = time.time()
+    r.render("composite")
+    torch.cuda.synchronize()
+    cold = time.time() - t0
+    st0 = vr.vr_get_stream_stats(r.ctx)
+    t0 = time.time()
+    r.render("composite")  # warm: the front bricks are cached
+    torch.cuda.synchronize()
+    warm = time.time() - t0
+    st = vr.vr_get_stream_stats(r.ctx)
+    r.close()
+    return {"workload": "4096x4096x8192 FP16 (256 GiB) streamed from the generator, 32 GiB cache, "
+                        "1920x1080, composite frame 0",
+            "cold_frame_s": cold, "warm_frame_s": warm, "bricks_fetched": st0["bricks_fetched"],
+            "bricks_culled": st0["bricks_culled"], "h2d_gb": st0["bytes_h2d"] / 1e9,
+            "generate_s": st0["generate_s"], "warm_refetched": st["bricks_fetched"] - st0["bricks_fetched"]}
 
 
 # ------------------------------------------------------------------------------ our arm
@@ -377,6 +515,18 @@ def run_ours(a):
     e1.record()
     torch.cuda.synchronize()
     res["ms_per_frame"]["composite"] = e0.elapsed_time(e1) / 5
+    if rank == 0 and not a.no_extras:
+        del rq, r32
+        torch.cuda.empty_cache()
+        res["extras"] = {}
+        for name, fn in (("wall", extra_wall), ("diff", extra_diff), ("ooc", extra_ooc)):
+            t0 = time.time()
+            try:
+                res["extras"][name] = fn(dev)
+            except Exception as exc:  # report, do not lose the main line
+                res["extras"][name] = {"error": f"{type(exc).__name__}: {exc}"}
+            res["extras"][name]["wall_s"] = time.time() - t0
+            torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
