@@ -108,6 +108,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate(times_ms, samples, world, device="cpu"):
+    """Whole-job figures over the ranks: the maximum of each time (the slowest rank
+    sets the job time) and the sum of the work.  world == 1 returns them unchanged."""
+    if world <= 1:
+        return list(times_ms), float(samples)
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    s = torch.tensor([float(samples)], dtype=torch.float64, device=device)
+    tdist.all_reduce(s, op=tdist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], float(s.item())
+
+
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
@@ -386,17 +400,8 @@ def run_ours(a):
     kernel_ms = [kev[i][0].elapsed_time(kev[i][1]) for i in range(a.steps)]
     ms32, samples32 = timed(r32)
 
-    # max over ranks
-    if world > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([ms, ms32], device=f"cuda:{dev}")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms, ms32 = float(t[0]), float(t[1])
-        s = torch.tensor([samples], dtype=torch.float64, device=f"cuda:{dev}")
-        tdist.all_reduce(s)
-        total_samples = float(s.item())
-    else:
-        total_samples = float(samples)
+    # max over ranks of the times, sum of the samples
+    (ms, ms32), total_samples = aggregate([ms, ms32], samples, world, f"cuda:{dev}")
 
     # end to end through the public API: camera from the host in, both images out to
     # pinned host memory, every step
@@ -416,11 +421,7 @@ def run_ours(a):
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([e2e_ms], device=f"cuda:{dev}")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_ms = float(t[0])
+    (e2e_ms,), _ = aggregate([e2e_ms], 0, world, f"cuda:{dev}")
 
     # roofline of the dominant kernel (the MIP brick pass)
     touch = load_touch_table()

@@ -35,6 +35,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "_oracle.so")
+# A prebuilt oracle library to load instead (the mutation test points this at
+# deliberately broken copies to show that the pins catch them).
+_LIB_OVERRIDE = os.environ.get("VR_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
@@ -72,8 +75,11 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+            if _LIB_OVERRIDE:
+                lib = ctypes.CDLL(_LIB_OVERRIDE)
+            else:
+                build()
+                lib = ctypes.CDLL(_LIB)
             lib.orc_render.restype = ctypes.c_int
             lib.orc_render.argtypes = [_P, _P, _P, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_int]
             lib.orc_render_sortlast.restype = ctypes.c_int

@@ -1,0 +1,75 @@
+"""The pins of test_oracle_pins.py must catch plausible mistakes in the oracle.
+
+Each case copies oracle.c, plants one mistake (on the CPU; nothing here touches a GPU),
+builds the copy, and runs the pin suite against it in a subprocess: the suite must fail."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "tf weight swapped": ("e->rgba[c] = (1.0 - w) * a + w * b;", "e->rgba[c] = w * a + (1.0 - w) * b;"),
+    "first sample floor": ("*k0 = (int64_t)ceil(a) + s->dk0;", "*k0 = (int64_t)floor(a) + s->dk0;"),
+    "last sample inclusive": ("*k1 = (int64_t)ceil(b) + s->dk1;", "*k1 = (int64_t)ceil(b) + 1 + s->dk1;"),
+    "colour without transmittance": ("for (int c = 0; c < 3; ++c) C[c] += T * a * e.rgba[c];",
+                                     "for (int c = 0; c < 3; ++c) C[c] += a * e.rgba[c];"),
+    "voxel centre offset dropped": ("double q = p[a] - 0.5;", "double q = p[a];"),
+    "axes swapped in the index": ("int64_t li = (z * s->ny + y) * s->nx + x;",
+                                  "int64_t li = (y * s->nz + z) * s->nx + x;"),
+    "termination before the crossing sample": (
+        "        for (int c = 0; c < 3; ++c) C[c] += T * a * e.rgba[c];\n        T *= (1.0 - a);\n"
+        "        if (s->ert <= 1.0 && fabs((1.0 - T) - s->ert) < 1e-5) r->flags |= FLAG_ERT;\n"
+        "        if (s->ert <= 1.0 && 1.0 - T >= s->ert) break;",
+        "        if (s->ert <= 1.0 && 1.0 - T * (1.0 - a) >= s->ert) break;\n"
+        "        for (int c = 0; c < 3; ++c) C[c] += T * a * e.rgba[c];\n        T *= (1.0 - a);"),
+    "perspective direction not normalised": ("for (int a = 0; a < 3; ++a) d[a] = dd[a] / len;",
+                                             "for (int a = 0; a < 3; ++a) d[a] = dd[a];"),
+    "pixel corner instead of centre": ("double u = l + ((double)px + 0.5) * (r - l) / (double)c->width;",
+                                       "double u = l + ((double)px) * (r - l) / (double)c->width;"),
+    "adjoint suffix sign": ("ga += g[c] * q->T * (q->rgb[c] - R[c]);", "ga += g[c] * q->T * (q->rgb[c] + R[c]);"),
+    "adjoint tf weight swapped": ("dtf[4 * q->e.i + c] += (1.0 - q->e.w) * gch[c];",
+                                  "dtf[4 * q->e.i + c] += q->e.w * gch[c];"),
+    "mip keeps the minimum": ("            if (v > m) m = v;\n            continue;", "            if (!(v > m) || m == -INFINITY) m = v;\n            continue;"),
+    "slab starts behind the eye": [("double lo = 0.0, hi = INFINITY;", "double lo = -INFINITY, hi = INFINITY;"),
+                                   ("    if (*k0 < 0) *k0 = 0;\n", "")],
+    "slab exit takes the farther plane": ("if (th < hi) hi = th;", "if (th > hi || hi == INFINITY) hi = th;"),
+    "sort-last folds back to front": ("if (x->key != y->key) return x->key < y->key ? -1 : 1;",
+                                      "if (x->key != y->key) return x->key < y->key ? 1 : -1;"),
+    "sort-last orthographic key sign": ("q->key += d[a] > 0 ? b[a] : (d[a] < 0 ? -b[a] : 0);",
+                                        "q->key += d[a] > 0 ? -b[a] : (d[a] < 0 ? b[a] : 0);"),
+    "sort-last perspective key unsigned distance": (
+        "q->key += b[a] > e[a] ? b[a] - e[a] : e[a] - b[a];", "q->key += b[a] - e[a];"),
+    "touch marks half the corners": ("for (int c = 0; c < 8; ++c) __atomic_store_n",
+                                     "for (int c = 0; c < 4; ++c) __atomic_store_n"),
+    "bf16 truncates": ("u = (u + 0x7fffu + lsb) & 0xffff0000u;", "u = u & 0xffff0000u;"),
+    "bf16 ties away from zero": ("u = (u + 0x7fffu + lsb) & 0xffff0000u;", "u = (u + 0x8000u) & 0xffff0000u;"),
+    "mip adjoint tf weight swapped": ("dtf[4 * e.i + c] += (1.0 - e.w) * g[c];", "dtf[4 * e.i + c] += e.w * g[c];"),
+    "adjoint suffix transmittance kept at one": ("        P *= (1.0 - q->a);\n", ""),
+    "adjoint colour gradient without opacity": ("gc[c] = g[c] * q->T * q->a;", "gc[c] = g[c] * q->T;"),
+    "tf slope where the lookup is clamped": (
+        "e->slope[c] = inside ? (b - a) * (double)(s->ntf - 1) / (s->vmax - s->vmin) : 0.0;",
+        "e->slope[c] = (b - a) * (double)(s->ntf - 1) / (s->vmax - s->vmin);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    sites = MUTANTS[name]
+    text = open(SRC).read()
+    for old, new in (sites if isinstance(sites, list) else [sites]):
+        assert text.count(old) == 1, f"mutation site not found once: {name}"
+        text = text.replace(old, new)
+    src = tmp_path / "oracle_mutant.c"
+    src.write_text(text)
+    lib = tmp_path / "oracle_mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-std=gnu11", "-ffp-contract=off",
+                           str(src), "-o", str(lib), "-lm"])
+    env = dict(os.environ, VR_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"the pins did not catch: {name}\n{r.stdout[-2000:]}"

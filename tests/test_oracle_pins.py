@@ -47,6 +47,12 @@ def test_constant_cube_closed_form(a):
         (cam(0, (-2, 3.3, -1), (s, 0, s), right=(s, 0, -s)), 23),
         # perspective along +z from z = -5.2: t in [5.2, 15.2) -> k = 11..30 (20 samples)
         (cam(1, (4, 3, -5.2), (0, 0, 1)), 20),
+        # perspective through an off-centre pixel, direction (-0.35, 0, 1), sec = sqrt(1.1225):
+        # enters z=0 at t = 5.2 sec = 5.509, leaves x=0 at depth 4/0.35, t = 12.108
+        # -> k = 12..24 (13 samples); an unnormalised direction would give 12
+        (cam(1, (4, 3, -5.2), (0, 0, 1), win=(-0.7, 0.0, -0.5, 0.5)), 13),
+        # perspective from inside the cube at z = 2.3 along +z: t in [0, 7.7) -> k = 0..15
+        (cam(1, (4, 3, 2.3), (0, 0, 1)), 16),
     ]
     for c, n in rays:
         sc = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5, ert=2.0)
@@ -281,6 +287,11 @@ def test_touch_census_axis_ray():
     m = oracle.touched(sc, cam(0, (1.5, 2.5, -0.7), (0, 0, 1)), "mip")
     want = np.zeros_like(m)
     want[:, 2:4, 1:3] = 1
+    assert np.array_equal(m, want)
+    # one ray along +x through (y, z) = (2.5, 1.5): corners y in {2,3}, z in {1,2}, every x
+    m = oracle.touched(sc, cam(0, (-0.7, 2.5, 1.5), (1, 0, 0), right=(0, 0, -1)), "mip")
+    want = np.zeros_like(m)
+    want[1:3, 2:4, :] = 1
     assert np.array_equal(m, want)
 
 
