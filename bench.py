@@ -49,6 +49,21 @@ def parse():
     return ap.parse_args()
 
 
+def workload_config(storage, world):
+    """The `config` of both arms' JSON lines.  The brick-store size follows the layout of
+    vr_load_cube: 128^3 bricks with a 1-voxel ghost, rows padded to 16 bytes, 256-byte slots."""
+    bpv = 2 if storage in ("f16", "bf16") else 4
+    rows = 130
+    pitch = -(-rows // (16 // bpv)) * (16 // bpv)
+    slot = -(-(rows * rows * pitch * bpv) // 256) * 256
+    store = slot * (1024 // 128) * (1024 // 128) * (2048 // 128)
+    return {"workload": "survey 1024x1024x2048 HI-like cube (2000 sources + ripple), "
+                        f"{storage} bricks 128^3+ghost, 1920x1080 perspective, "
+                        "36-frame orbit, step 0.5, composite (ERT 0.99) + MIP per step",
+            "storage": storage, "compute": "f32", "parallelism": f"replicas x{world}",
+            "l2": f"inputs larger than L2 ({store / 1e9:.2f} GB store)"}
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -454,11 +469,7 @@ def run_ours(a):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "survey 1024x1024x2048 HI-like cube (2000 sources + ripple), "
-                               f"{a.storage} bricks 128^3+ghost, 1920x1080 perspective, "
-                               "36-frame orbit, step 0.5, composite (ERT 0.99) + MIP per step",
-                   "storage": a.storage, "compute": "f32", "parallelism": f"replicas x{world}",
-                   "l2": f"inputs larger than L2 ({info['store_bytes'] / 1e9:.2f} GB store)"},
+        "config": workload_config(a.storage, world),
         "ms_per_frame": {"composite": None, "mip_brick_kernel": mip_ms},
         "rays_per_s": W * H * 2 * a.steps / (ms / 1e3) * world,
         "fp32_path": {"ms_per_step": ms32 / a.steps,
@@ -576,9 +587,7 @@ def run_reference(a):
            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": dt * 1e3 / a.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "survey 1024x1024x2048 HI-like cube, 1920x1080 perspective "
-                                  "orbit, step 0.5, composite (ERT 0.99) + MIP",
-                      "storage": a.storage},
+           "config": workload_config(a.storage, world),
            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": os.cpu_count(),
                             "kind": "oracle",
                             "sample": f"{npix} seeded pixels per step (central band), "
