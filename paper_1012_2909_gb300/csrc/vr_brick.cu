@@ -26,9 +26,12 @@ namespace vr {
 
 namespace {
 
-constexpr int kBrickThreads = 256;  // two CTAs per SM
-constexpr int kSegCap = 512;        // segment records per chunk
-constexpr int kUnroll = 1;  // samples per lane per step (more overlap measured slower)
+// Two CTAs of 512 threads per SM: 32 warps at the 64-register limit (the march
+// is latency-bound; 256-thread CTAs were 9-11 % slower).
+constexpr int kBrickThreads = 512;
+constexpr int kSegCap = 512;  // segment records per chunk
+static_assert(kSegCap % kBrickThreads == 0, "segment chunk must be a multiple of the CTA size");
+constexpr int kUnroll = 1;  // samples per lane per step (2 measured no faster)
 
 template <typename T> struct Cell;
 template <> struct Cell<float> {
@@ -380,13 +383,19 @@ __device__ __forceinline__ float group_max(const T* __restrict__ tile, const Seg
     return m;
 }
 
+// Warps claim batches of 32/G records from a shared counter, so that the
+// barrier at the end of a chunk waits for at most one batch per warp.
 template <typename T, int G, int U>
 __device__ __forceinline__ void march_segments(const BrickParams& P, const T* tile, const SegRec* segs,
-                                               int nseg, int warp, int lane) {
+                                               int nseg, int* claim, int lane) {
     constexpr int PER_WARP = 32 / G;
     const int q = lane / G, r = lane % G;
     const unsigned int gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (q * G);
-    for (int s0 = warp * PER_WARP; s0 < nseg; s0 += (kBrickThreads / 32) * PER_WARP) {
+    for (;;) {
+        int s0 = 0;
+        if (lane == 0) s0 = atomicAdd(claim, PER_WARP);
+        s0 = __shfl_sync(0xffffffffu, s0, 0);
+        if (s0 >= nseg) break;
         // groups past the end of the list repeat the last record (no atomics)
         const int si = min(s0 + q, nseg - 1);
         const SegRec s = segs[si];
@@ -422,6 +431,7 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     __shared__ int4 s_rect[3][kMaxLaunchCams];
     __shared__ int s_u[3];
     __shared__ int s_cnt[2];
+    __shared__ int s_claim[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nvalid = *count;
@@ -472,6 +482,7 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
             fence_mbar_init();
             s_cnt[0] = 0;
             s_cnt[1] = 0;
+            s_claim[0] = 0;
         }
         claim(0);
         if (s_u[0] < nvalid) {
@@ -492,8 +503,11 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     if (!__syncthreads_and(ok)) return;  // no copy is in flight after a failed wait of the only load
     for (;;) {
         const int nseg = s_cnt[chunk & 1];
-        if (tid == 0) s_cnt[(chunk + 1) & 1] = 0;
-        march_segments<T, GROUP, kUnroll>(P, tile, segs, nseg, warp, lane);
+        if (tid == 0) {
+            s_cnt[(chunk + 1) & 1] = 0;
+            s_claim[(chunk + 1) & 1] = 0;
+        }
+        march_segments<T, GROUP, kUnroll>(P, tile, segs, nseg, &s_claim[chunk & 1], lane);
         __syncthreads();
         ++chunk;
         c0 += kSegCap;
