@@ -72,6 +72,7 @@ struct vr_ctx {
     int* work = nullptr;
     int work_slots = 0;
     int2* krange = nullptr;        // per-pixel sample range of the brick pass
+    float4* pixdir = nullptr;      // per-pixel float-float step vector (2 x float4)
     unsigned int* enc = nullptr;   // per-pixel running maximum when out_max is NULL
     long long scratch_pix = 0;
     // sort-last / layered scratch
@@ -346,6 +347,7 @@ vr_status vr_destroy(vr_ctx* ctx) {
         free_cube(ctx);
         if (ctx->work) cudaFree(ctx->work);
         if (ctx->krange) cudaFree(ctx->krange);
+        if (ctx->pixdir) cudaFree(ctx->pixdir);
         if (ctx->enc) cudaFree(ctx->enc);
         if (ctx->tf_partials) cudaFree(ctx->tf_partials);
         for (void* p : {(void*)ctx->foot, (void*)ctx->order, (void*)ctx->tile_start, (void*)ctx->layer_buf,
@@ -677,11 +679,14 @@ vr_status render_ray(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
 vr_status ensure_pixel_scratch(vr_ctx* ctx, long long npix) {
     if (npix <= ctx->scratch_pix) return VR_OK;
     if (ctx->krange) cudaFree(ctx->krange);
+    if (ctx->pixdir) cudaFree(ctx->pixdir);
     if (ctx->enc) cudaFree(ctx->enc);
     ctx->krange = nullptr;
+    ctx->pixdir = nullptr;
     ctx->enc = nullptr;
     ctx->scratch_pix = 0;
     VR_CK(cudaMalloc(&ctx->krange, sizeof(int2) * npix), "vr_render: pixel scratch");
+    VR_CK(cudaMalloc(&ctx->pixdir, 2 * sizeof(float4) * npix), "vr_render: pixel scratch");
     VR_CK(cudaMalloc(&ctx->enc, sizeof(unsigned int) * npix), "vr_render: pixel scratch");
     ctx->scratch_pix = npix;
     return VR_OK;
@@ -717,6 +722,7 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
     bp.ncells_z = ctx->B / cz;
     bp.nbricks = ctx->nbx * ctx->nby * ctx->nbz;
     bp.krange = ctx->krange;
+    bp.pixdir = ctx->pixdir;
     bp.status = ctx->status_dev;
     const int grid = 2 * ctx->num_sms;
     for (int c0 = 0; c0 < ncams; c0 += per) {
@@ -728,6 +734,7 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
                 return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: camera basis is singular");
             pp.cam = ctx->cams[(size_t)(c0 + i)];
             pp.krange = ctx->krange + (long long)i * img;
+            pp.pixdir = ctx->pixdir + 2 * (long long)i * img;
             pp.enc = enc + (long long)i * img;
             VR_CK(launch_pixel_setup(pp, s), "vr_render: pixel set-up");
         }
@@ -1077,6 +1084,7 @@ vr_status render_ooc(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
     pp.width = W;
     pp.height = H;
     pp.krange = ctx->krange;
+    pp.pixdir = ctx->pixdir;
     BrickParams bp;
     std::memset(&bp, 0, sizeof(bp));
     bp.vol = sp.vol;
@@ -1091,6 +1099,7 @@ vr_status render_ooc(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
     bp.ncells_z = ctx->B / cz;
     bp.nbricks = ctx->nbx * ctx->nby * ctx->nbz;
     bp.krange = ctx->krange;
+    bp.pixdir = ctx->pixdir;
     bp.status = ctx->status_dev;
     std::vector<int> order, layer_start, list;
     std::vector<BrickFoot> foot;

@@ -70,6 +70,22 @@ template <> __device__ __forceinline__ float cvt<__nv_bfloat16>(__nv_bfloat16 v)
     return __bfloat162float(v);
 }
 
+// (float)a - b with one rounding.  For 16-bit a this is the mixed-precision
+// form of sub (the operand is widened exactly), one instruction instead of a
+// conversion and an FP32 subtraction, with the same result.
+template <typename T> __device__ __forceinline__ float sub_wide(T a, float b);
+template <> __device__ __forceinline__ float sub_wide<float>(float a, float b) { return a - b; }
+template <> __device__ __forceinline__ float sub_wide<__half>(__half a, float b) {
+    float d;
+    asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(a)), "f"(b));
+    return d;
+}
+template <> __device__ __forceinline__ float sub_wide<__nv_bfloat16>(__nv_bfloat16 a, float b) {
+    float d;
+    asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(a)), "f"(b));
+    return d;
+}
+
 // Trilinear fetch from a staged cell; g in tile coordinates (lower corner
 // floor(g), 0 = ghost).  CLAMP keeps every access inside the tile; without it
 // the caller guarantees 0 <= g < extent + 1 on every axis.
@@ -85,12 +101,12 @@ __device__ __forceinline__ float tile_fetch(const T* __restrict__ t, float gx, f
     const float fx = gx - x0, fy = gy - y0, fz = gz - z0;
     const int i = (int)fmaf(fmaf(z0, (float)C::BY, y0), (float)C::BX, x0);
     constexpr int SY = C::BX, SZ = C::BX * C::BY;
-    const float c000 = cvt<T>(t[i]), c100 = cvt<T>(t[i + 1]);
-    const float c010 = cvt<T>(t[i + SY]), c110 = cvt<T>(t[i + SY + 1]);
-    const float c001 = cvt<T>(t[i + SZ]), c101 = cvt<T>(t[i + SZ + 1]);
-    const float c011 = cvt<T>(t[i + SZ + SY]), c111 = cvt<T>(t[i + SZ + SY + 1]);
-    const float a0 = fmaf(fx, c100 - c000, c000), a1 = fmaf(fx, c110 - c010, c010);
-    const float a2 = fmaf(fx, c101 - c001, c001), a3 = fmaf(fx, c111 - c011, c011);
+    const float c000 = cvt<T>(t[i]), c010 = cvt<T>(t[i + SY]);
+    const float c001 = cvt<T>(t[i + SZ]), c011 = cvt<T>(t[i + SZ + SY]);
+    const float a0 = fmaf(fx, sub_wide<T>(t[i + 1], c000), c000);
+    const float a1 = fmaf(fx, sub_wide<T>(t[i + SY + 1], c010), c010);
+    const float a2 = fmaf(fx, sub_wide<T>(t[i + SZ + 1], c001), c001);
+    const float a3 = fmaf(fx, sub_wide<T>(t[i + SZ + SY + 1], c011), c011);
     const float b0 = fmaf(fy, a1 - a0, a0), b1 = fmaf(fy, a3 - a2, a2);
     return fmaf(fz, b1 - b0, b0);
 }
@@ -172,7 +188,7 @@ __device__ __forceinline__ bool cam_cell_rect(const CamFF& c, float3 lo, int4& r
 // the ray owns no sample there.
 template <typename T>
 __device__ __forceinline__ bool make_segment(const BrickParams& P, const CamFF& c, int px, int py,
-                                             int2 kr, float3 lo, SegRec& s) {
+                                             int2 kr, float3 lo, const float4* pd, SegRec& s) {
     using C = Cell<T>;
     const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
     float o[3], e[3];
@@ -230,7 +246,14 @@ __device__ __forceinline__ bool make_segment(const BrickParams& P, const CamFF& 
     if (ka >= kb) return false;
     // float-float anchor of sample ka
     ff E[3], O[3];
-    if (c.type == 1) {
+    if (c.type == 1 && pd) {  // step vector from the pixel set-up (FP64, split)
+        const float4 d0 = pd[0], d1 = pd[1];
+        E[0] = ff{d0.x, d0.w};
+        E[1] = ff{d0.y, d1.x};
+        E[2] = ff{d0.z, d1.y};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) O[a] = ff{c.org_hi[a], c.org_lo[a]};
+    } else if (c.type == 1) {
         ff V[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -333,25 +356,37 @@ __device__ __forceinline__ void build_segments(const BrickParams& P, int cam_, i
     const CamFF& c = P.cams[cam];
     const long long img = (long long)P.width * P.height;
     const int2* kr_img = P.krange + (long long)cam * img;
+    const float4* pd_img = P.pixdir ? P.pixdir + 2 * (long long)cam * img : nullptr;
     const int rw = rect.z - rect.x + 1;
     const int npx = rw * (rect.w - rect.y + 1);
     const int c1 = min(npx, c0 + kSegCap);
+    const float inv_rw = 1.0f / (float)rw;
     constexpr int PER = kSegCap / kBrickThreads;
     int2 kr[PER];
     int pxv[PER], pyv[PER];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
         const int i = c0 + tid + q * kBrickThreads;
+        // row i / rw from a float reciprocal (off by at most one), then corrected
+        int row = (int)(((float)i + 0.5f) * inv_rw), col = i - row * rw;
+        if (col < 0) {
+            --row;
+            col += rw;
+        } else if (col >= rw) {
+            ++row;
+            col -= rw;
+        }
         kr[q] = make_int2(0, 0);
-        pyv[q] = rect.y + i / rw;
-        pxv[q] = rect.x + i % rw;
+        pyv[q] = rect.y + row;
+        pxv[q] = rect.x + col;
         if (i < c1) kr[q] = kr_img[pyv[q] * P.width + pxv[q]];
     }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
         if (kr[q].x >= kr[q].y) continue;
         SegRec s;
-        if (make_segment<T>(P, c, pxv[q], pyv[q], kr[q], lo, s)) {
+        const float4* pd = pd_img ? pd_img + 2 * ((long long)pyv[q] * P.width + pxv[q]) : nullptr;
+        if (make_segment<T>(P, c, pxv[q], pyv[q], kr[q], lo, pd, s)) {
             s.pix += (int)(cam * img);
             segs[atomicAdd(cnt, 1)] = s;
         }
@@ -369,12 +404,13 @@ template <typename T, int G, int U, bool CLAMP>
 __device__ __forceinline__ float group_max(const T* __restrict__ tile, const SegRec& s, int n, int r,
                                            int iters) {
     float m = -INFINITY;
-    const int last = n - 1;
-    for (int it = 0; it < iters; ++it) {
+    const float last = (float)(n - 1);
+    float fr = (float)r;  // sample index of this lane (integers < 2^24 are exact)
+    for (int it = 0; it < iters; ++it, fr += (float)(U * G)) {
         float v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const float f = (float)min(it * U * G + u * G + r, last);
+            const float f = fminf(fr + (float)(u * G), last);
             v[u] = tile_fetch<T, CLAMP>(tile, fmaf(f, s.ex, s.gx), fmaf(f, s.ey, s.gy), fmaf(f, s.ez, s.gz));
         }
 #pragma unroll
@@ -538,9 +574,19 @@ __global__ void k_pixel_setup(const __grid_constant__ PixelParams P) {
     const int n = P.width * P.height;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         Ray r;
-        make_ray(P.cam, i % P.width, i / P.width, P.vol, P.step, r);
+        const bool hit = make_ray(P.cam, i % P.width, i / P.width, P.vol, P.step, r);
         P.krange[i] = make_int2(r.k0, r.k1);
         P.enc[i] = ord_enc(-INFINITY);
+        if (hit && P.pixdir && P.cam.type == 1) {  // read only for pixels with samples
+            float h[3], l[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                h[a] = (float)r.e[a];
+                l[a] = (float)(r.e[a] - (double)h[a]);
+            }
+            P.pixdir[2 * (long long)i] = make_float4(h[0], h[1], h[2], l[0]);
+            P.pixdir[2 * (long long)i + 1] = make_float4(l[1], l[2], 0.f, 0.f);
+        }
     }
 }
 

@@ -84,6 +84,9 @@ struct BrickParams {
     int ncells_x, ncells_y, ncells_z;  // cells per brick along each axis
     int nbricks;
     const int2* krange;      // per pixel [k0, k1) from the double-precision set-up
+    const float4* pixdir;    // optional, perspective cameras: per pixel the step
+                             // vector e in float-float, 2 x float4 (hi.xyz, lo.x),
+                             // (lo.y, lo.z, -, -), written by the pixel set-up
     unsigned int* out_enc;   // per pixel ordered-int encoding of the running maximum
     const int* brick_list;   // optional: only the cells of these bricks (out-of-core batches)
     int nlist, pad_l;
@@ -150,6 +153,7 @@ struct PixelParams {
     double step;
     int width, height;
     int2* krange;
+    float4* pixdir;  // optional: per-pixel float-float step vector (see BrickParams)
     unsigned int* enc;
     float4* out_rgba;
     float* out_max;
