@@ -200,7 +200,8 @@ def _events_ms(fn, reps):
 def extra_wall(dev):
     """5 x 5 wall of 1920 x 1080 panels (25 off-axis frusta of one camera) on the
     2048 x 2048 x 1024 FP16 cube: batched (one graph launch per mode, autotuned)
-    versus the 25 panels rendered one by one."""
+    versus the 25 panels rendered one by one, on the FP16 store and on the plain
+    FP32 store with default launch shapes."""
     import torch
 
     import paper_1012_2909_gb300 as vr
@@ -212,7 +213,6 @@ def extra_wall(dev):
     vol = synth.generate(p)
     r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
     r.load_cube(vol, "f16")
-    del vol
     r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
     big = synth.orbit_view(dims, 30.0, 5 * W, 5 * H)
     panels = synth.wall_views(big, 5, 5)
@@ -246,7 +246,65 @@ def extra_wall(dev):
         out[f"{mode}_samples_per_s"] = out[f"{mode}_samples"] / (out[f"{mode}_batched_ms"] / 1e3)
         out[f"{mode}_batching_speedup"] = out[f"{mode}_25_single_ms"] / out[f"{mode}_batched_ms"]
     out["tuning"] = {m: {k: v for k, v in t.items() if k != "cached"} for m, t in tune.items()}
-    out["workload"] = "2048x2048x1024 FP16, 25 x 1920x1080 off-axis frusta (9600x5400), graph mode"
+    r.close()
+    # the plain FP32 single-view path on the same panels
+    r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
+    r.load_cube(vol, "f32")
+    del vol
+    r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
+    for mode in ("composite", "mip"):
+        def singles32():
+            for c in panels:
+                r.set_camera(c)
+                r.render(mode, out=one)
+        singles32()  # first use allocates the per-pixel scratch
+        out[f"{mode}_fp32_25_single_ms"] = _events_ms(singles32, 1)
+        out[f"{mode}_speedup_vs_fp32_single"] = out[f"{mode}_fp32_25_single_ms"] / out[f"{mode}_batched_ms"]
+    r.close()
+    out["workload"] = ("2048x2048x1024 FP16, 25 x 1920x1080 off-axis frusta (9600x5400), graph mode; "
+                       "baseline: FP32 store, one panel per render, default launch shapes")
+    return out
+
+
+def extra_hipass(dev):
+    """High-resolution static render (one orientation) of the paper's HIPASS-shaped cube,
+    1721 x 1721 x 1025 FP32, at 3000 x 3000 and 8000 x 8000: MIP (brick pass) and
+    composite (image order, termination 0.99)."""
+    import torch
+
+    import paper_1012_2909_gb300 as vr
+    import synth
+    cfg = synth.CONFIGS["hipass"]
+    p = cfg["cube"]
+    dims = (p["nx"], p["ny"], p["nz"])
+    vol = synth.generate(p)
+    r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
+    r.load_cube(vol, "f32")
+    del vol
+    r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
+    counter = torch.zeros(1, dtype=torch.int64, device=f"cuda:{dev}")
+    out = {"workload": "1721x1721x1025 FP32 (HIPASS shape, 2830 sources + ripple), perspective, "
+                       "one orientation, step 0.5"}
+    for W, H in cfg["images"]:
+        r.set_camera(synth.orbit_view(dims, cfg["az"], W, H))
+        img = torch.empty((1, H, W, 4), device=f"cuda:{dev}")
+        res = {}
+        for mode in ("composite", "mip"):
+            r.set_path("ray")
+            vr.vr_set_sample_counter(r.ctx, counter)
+            counter.zero_()
+            r.render(mode, out=img)
+            torch.cuda.synchronize()
+            n = int(counter.item())
+            vr.vr_set_sample_counter(r.ctx, None)
+            r.set_path("auto")
+            r.render(mode, out=img)
+            ms = _events_ms(lambda: r.render(mode, out=img), 3)
+            res[f"{mode}_ms"] = ms
+            res[f"{mode}_samples"] = n
+            res[f"{mode}_samples_per_s"] = n / (ms / 1e3)
+        out[f"{W}x{H}"] = res
+        del img
     r.close()
     return out
 
@@ -531,7 +589,8 @@ def run_ours(a):
         del rq, r32
         torch.cuda.empty_cache()
         res["extras"] = {}
-        for name, fn in (("wall", extra_wall), ("diff", extra_diff), ("ooc", extra_ooc)):
+        for name, fn in (("wall", extra_wall), ("hipass", extra_hipass), ("diff", extra_diff),
+                         ("ooc", extra_ooc)):
             t0 = time.time()
             try:
                 res["extras"][name] = fn(dev)

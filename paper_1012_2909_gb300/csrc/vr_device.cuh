@@ -59,18 +59,22 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, const 
         }
         if (!(lo32 <= hi32 * 1.0001f + 1e-3f)) return false;
     }
-    const double len = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+    // Reciprocals instead of divisions (double-precision division is slow on this
+    // part): t_near and t_far move by a few ulps, far inside the tolerance at which
+    // a sample range is treated as ambiguous.
+    const double inv_len = 1.0 / sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
     const double n[3] = {(double)v.nx, (double)v.ny, (double)v.nz};
     double lo = 0.0, hi = 1e300;
     bool hit = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double d = dd[a] / len;
+        const double d = dd[a] * inv_len;
         r.e[a] = d * step;
         if (d == 0.0) {
             if (r.o[a] < 0.0 || r.o[a] > n[a]) hit = false;
         } else {
-            const double t1 = (0.0 - r.o[a]) / d, t2 = (n[a] - r.o[a]) / d;
+            const double inv_d = 1.0 / d;
+            const double t1 = (0.0 - r.o[a]) * inv_d, t2 = (n[a] - r.o[a]) * inv_d;
             lo = fmax(lo, fmin(t1, t2));
             hi = fmin(hi, fmax(t1, t2));
         }

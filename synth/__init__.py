@@ -119,6 +119,12 @@ CONFIGS = {
     "diff": dict(cube=cube_params(256, 256, 256, seed=1238, nsrc=50),
                  image=(512, 512), views=64, view_seed=7, tf_seed=99, step=0.5, ert=0.99,
                  storage=("f32",)),
+    # The paper's HIPASS cube shape (Sec. 3: 1721 x 1721 x 1025, 32-bit floats, 12 GB), same
+    # source density as the survey (2830 sources); one perspective orientation rendered as a
+    # high-resolution static image at 3000 x 3000 and 8000 x 8000.
+    "hipass": dict(cube=cube_params(1721, 1721, 1025, seed=1240, nsrc=2830, ripple=True),
+                   images=((3000, 3000), (8000, 8000)), az=30.0, step=0.5, ert=0.99,
+                   storage=("f32",)),
     # 4096 x 4096 x 8192 FP16, same source model (density-scaled: 128000 sources),
     # streamed out of core; 1920 x 1080 perspective, 10-frame orbit.
     "ooc": dict(cube=cube_params(4096, 4096, 8192, seed=1239, nsrc=128000, ripple=True),
