@@ -17,7 +17,8 @@ formulas, so each step is the standard definition):
 5. node-centred linear transfer-function lookup over [vmin, vmax], clamped;
 6. front-to-back "over" with termination after the sample at which
    1 - T >= ert; MIP outputs TF(max v) straight;
-7. the adjoint of 6 (reverse sweep with suffix colour / transmittance).
+7. the adjoint of 6 (reverse sweep with suffix colour / transmittance);
+8. the image pyramid of a render (2 x 2 box filter of premultiplied RGBA per level).
 
 Parity pins: see tests/test_oracle_pins.py (closed forms for constant cubes,
 single-peak MIP, brute force along the spectral axis, sort-last invariance,
@@ -91,6 +92,9 @@ def _load():
             lib.orc_touch.argtypes = [_P, _P, _P, ctypes.c_int64, _P, ctypes.c_int]
             lib.orc_round_bf16.restype = None
             lib.orc_round_bf16.argtypes = [_P, _P, ctypes.c_int64]
+            lib.orc_pyramid.restype = ctypes.c_int
+            lib.orc_pyramid.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P,
+                                        ctypes.POINTER(ctypes.c_int64)]
             _lib = lib
     return _lib
 
@@ -234,6 +238,33 @@ def round_storage(vol: np.ndarray, storage: str) -> np.ndarray:
         _load().orc_round_bf16(_ptr(vol), _ptr(out), vol.size)
         return out
     raise ValueError(storage)
+
+
+def pyramid(img: np.ndarray, tile: int = 0):
+    """Levels 1.. of a premultiplied RGBA image (H, W, 4): each level halves the size
+    (rounding up) and averages the pixels of each 2 x 2 block that lie inside the level.
+    Returns (number of levels counting the input, packed levels as float64, row-major or
+    in tile x tile tiles -- the layout of vr_image_pyramid)."""
+    a = np.ascontiguousarray(img, dtype=np.float32)
+    assert a.ndim == 3 and a.shape[2] == 4
+    h, w = a.shape[:2]
+    lib = _load()
+    n = ctypes.c_int64(0)
+    levels = lib.orc_pyramid(_ptr(a), w, h, int(tile), None, ctypes.byref(n))
+    if levels < 0:
+        raise ValueError("orc_pyramid: bad arguments")
+    out = np.zeros(n.value, np.float64)
+    lib.orc_pyramid(_ptr(a), w, h, int(tile), _ptr(out), ctypes.byref(n))
+    return levels, out
+
+
+def pyramid_sizes(w: int, h: int):
+    """(width, height) of levels 1.. (down to 1 x 1)."""
+    out = []
+    while w > 1 or h > 1:
+        w, h = (w + 1) // 2, (h + 1) // 2
+        out.append((w, h))
+    return out
 
 
 def l2_loss(img: np.ndarray, target: np.ndarray):

@@ -686,3 +686,81 @@ void orc_round_bf16(const float* in, float* out, int64_t n)
         memcpy(&out[i], &u, 4);
     }
 }
+
+/* ------------------------------------------------------------ image pyramid */
+/*
+ * Levels of a premultiplied RGBA image for viewers that show a high-resolution
+ * render at several zoom levels (Sec. 3: static renders of one orientation at
+ * user-chosen sizes, cut into tiles for display).  Level 0 is the image,
+ * W x H; level l+1 is ceil(W_l / 2) x ceil(H_l / 2), and its pixel (x, y) is
+ * the mean of the pixels (2x + i, 2y + j), i, j in {0, 1}, of level l that lie
+ * inside level l (one, two or four of them).  Premultiplied colour makes this
+ * box filter the right one for alpha.
+ *
+ * Output: levels 1 .. L-1 (L = number of levels down to 1 x 1, counting level
+ * 0) one after the other, 4 doubles a pixel, each level either row-major
+ * (tile = 0) or as ceil(W/tile) x ceil(H/tile) tiles of tile x tile pixels,
+ * tiles row-major, pixels row-major inside a tile, with zeros where a tile
+ * passes the level's edge.  Returns the number of levels L, or -1 on bad
+ * arguments.  out may be NULL to size it: *nout receives the doubles needed.
+ */
+static int64_t pyr_level_pixels(int64_t w, int64_t h, int64_t tile)
+{
+    if (tile <= 0) return w * h;
+    int64_t tx = (w + tile - 1) / tile, ty = (h + tile - 1) / tile;
+    return tx * ty * tile * tile;
+}
+
+static int64_t pyr_index(int64_t x, int64_t y, int64_t w, int64_t tile)
+{
+    if (tile <= 0) return y * w + x;
+    int64_t tx = (w + tile - 1) / tile;
+    return ((y / tile) * tx + x / tile) * tile * tile + (y % tile) * tile + (x % tile);
+}
+
+int orc_pyramid(const float* img, int64_t w, int64_t h, int64_t tile, double* out, int64_t* nout)
+{
+    if (w <= 0 || h <= 0 || tile < 0) return -1;
+    int levels = 1;
+    int64_t total = 0;
+    for (int64_t lw = w, lh = h; lw > 1 || lh > 1;) {
+        lw = (lw + 1) / 2;
+        lh = (lh + 1) / 2;
+        total += 4 * pyr_level_pixels(lw, lh, tile);
+        ++levels;
+    }
+    if (nout) *nout = total;
+    if (!out) return levels;
+    memset(out, 0, sizeof(double) * (size_t)total);
+    /* the previous level, row-major, in double */
+    double* prev = (double*)malloc(sizeof(double) * 4 * (size_t)(w * h));
+    for (int64_t i = 0; i < 4 * w * h; ++i) prev[i] = (double)img[i];
+    int64_t pw = w, ph = h, off = 0;
+    while (pw > 1 || ph > 1) {
+        int64_t lw = (pw + 1) / 2, lh = (ph + 1) / 2;
+        double* cur = (double*)malloc(sizeof(double) * 4 * (size_t)(lw * lh));
+        for (int64_t y = 0; y < lh; ++y)
+            for (int64_t x = 0; x < lw; ++x) {
+                double acc[4] = {0, 0, 0, 0};
+                int n = 0;
+                for (int j = 0; j < 2; ++j)
+                    for (int i = 0; i < 2; ++i) {
+                        int64_t sx = 2 * x + i, sy = 2 * y + j;
+                        if (sx >= pw || sy >= ph) continue;
+                        for (int c = 0; c < 4; ++c) acc[c] += prev[4 * (sy * pw + sx) + c];
+                        ++n;
+                    }
+                for (int c = 0; c < 4; ++c) {
+                    cur[4 * (y * lw + x) + c] = acc[c] / (double)n;
+                    out[off + 4 * pyr_index(x, y, lw, tile) + c] = acc[c] / (double)n;
+                }
+            }
+        off += 4 * pyr_level_pixels(lw, lh, tile);
+        free(prev);
+        prev = cur;
+        pw = lw;
+        ph = lh;
+    }
+    free(prev);
+    return levels;
+}

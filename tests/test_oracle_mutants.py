@@ -53,6 +53,10 @@ MUTANTS = {
     "tf slope where the lookup is clamped": (
         "e->slope[c] = inside ? (b - a) * (double)(s->ntf - 1) / (s->vmax - s->vmin) : 0.0;",
         "e->slope[c] = (b - a) * (double)(s->ntf - 1) / (s->vmax - s->vmin);"),
+    "pyramid divides by four at edges": ("cur[4 * (y * lw + x) + c] = acc[c] / (double)n;",
+                                         "cur[4 * (y * lw + x) + c] = acc[c] / 4.0;"),
+    "pyramid tiles transposed": ("return ((y / tile) * tx + x / tile) * tile * tile + (y % tile) * tile + (x % tile);",
+                                 "return ((x / tile) * tx + y / tile) * tile * tile + (y % tile) * tile + (x % tile);"),
 }
 
 

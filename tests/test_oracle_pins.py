@@ -308,3 +308,68 @@ def test_bf16_rounding():
     assert np.array_equal(oracle.round_storage(y, "bf16"), want)
     assert np.array_equal(oracle.round_storage(y, "f16"),
                           torch.from_numpy(y).to(torch.float16).to(torch.float32).numpy())
+
+
+# ---------------------------------------------------------------------- image pyramid
+def test_pyramid_hand_example_3x3():
+    rng = np.random.default_rng(3)
+    a32 = rng.random((3, 3, 4)).astype(np.float32)
+    a = a32.astype(np.float64)
+    levels, out = oracle.pyramid(a32)
+    assert levels == 3 and out.size == 4 * (4 + 1)
+    want1 = np.array([[(a[0, 0] + a[0, 1] + a[1, 0] + a[1, 1]) / 4, (a[0, 2] + a[1, 2]) / 2],
+                      [(a[2, 0] + a[2, 1]) / 2, a[2, 2]]])
+    np.testing.assert_allclose(out[:16].reshape(2, 2, 4), want1, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(out[16:], want1.reshape(4, 4).mean(axis=0), rtol=0, atol=1e-15)
+
+
+def test_pyramid_constant_image_and_level_count():
+    c = np.array([0.1, 0.2, 0.3, 0.7], np.float32)
+    for h, w in ((13, 7), (1, 9), (6, 1), (1, 1)):
+        levels, out = oracle.pyramid(np.tile(c, (h, w, 1)))
+        # levels: ceil(log2(max(w, h))) + 1
+        assert levels == int(np.ceil(np.log2(max(w, h)))) + 1
+        assert np.array_equal(out.reshape(-1, 4), np.tile(c.astype(np.float64), (out.size // 4, 1)))
+
+
+def test_pyramid_power_of_two_block_means():
+    rng = np.random.default_rng(4)
+    a = rng.random((32, 16, 4)).astype(np.float32)  # H = 32, W = 16
+    levels, out = oracle.pyramid(a)
+    assert levels == 6
+    lev = a.astype(np.float64)
+    off = 0
+    for w, h in oracle.pyramid_sizes(16, 32):
+        lh, lw = lev.shape[:2]
+        # 2 x 2 block means where both sides are even; a side of 1 averages the pairs of the other
+        nxt = lev.reshape(lh // 2 if lh > 1 else 1, 2 if lh > 1 else 1,
+                          lw // 2 if lw > 1 else 1, 2 if lw > 1 else 1, 4).mean(axis=(1, 3))
+        got = out[off:off + 4 * w * h].reshape(h, w, 4)
+        np.testing.assert_allclose(got, nxt, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(got.mean(axis=(0, 1)), a.astype(np.float64).mean(axis=(0, 1)),
+                                   rtol=0, atol=1e-12)  # the mean is preserved
+        off += 4 * w * h
+        lev = nxt
+    assert off == out.size
+
+
+def test_pyramid_tiled_layout():
+    rng = np.random.default_rng(5)
+    a = rng.random((6, 10, 4)).astype(np.float32)  # H = 6, W = 10
+    _, flat = oracle.pyramid(a, tile=0)
+    _, tiled = oracle.pyramid(a, tile=4)
+    off_f = off_t = 0
+    for w, h in oracle.pyramid_sizes(10, 6):
+        lev = flat[off_f:off_f + 4 * w * h].reshape(h, w, 4)
+        tx, ty = -(-w // 4), -(-h // 4)
+        blk = tiled[off_t:off_t + 4 * tx * ty * 16].reshape(ty * tx, 4, 4, 4)
+        for y in range(4 * ty):
+            for x in range(4 * tx):
+                v = blk[(y // 4) * tx + x // 4, y % 4, x % 4]
+                if x < w and y < h:
+                    assert np.array_equal(v, lev[y, x])
+                else:
+                    assert not v.any()  # padding of edge tiles
+        off_f += 4 * w * h
+        off_t += 4 * tx * ty * 16
+    assert off_f == flat.size and off_t == tiled.size
