@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--storage", default="f16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile", choices=["mip", "composite", "both"], default=None,
+    ap.add_argument("--profile", choices=["mip", "composite", "both", "pyramid"], default=None,
                     help="only render --warmup + --steps orbit frames (for ncu); no timing legs")
     ap.add_argument("--cube", default=None,
                     help="NX,NY,NZ: override the cube size (same source density) for small captures")
@@ -266,6 +266,14 @@ def extra_wall(dev):
     return out
 
 
+def _measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("hbm_gbs", 6800.0))
+    except OSError:
+        return 6800.0
+
+
 def extra_hipass(dev):
     """High-resolution static render (one orientation) of the paper's HIPASS-shaped cube,
     1721 x 1721 x 1025 FP32, at 3000 x 3000 and 8000 x 8000: MIP (brick pass) and
@@ -303,6 +311,24 @@ def extra_hipass(dev):
             res[f"{mode}_ms"] = ms
             res[f"{mode}_samples"] = n
             res[f"{mode}_samples_per_s"] = n / (ms / 1e3)
+        if W * H >= 64_000_000:
+            # pyramid of the composite render: HBM-bound; algorithmic bytes = level 0 read once
+            # plus every level written once (edge-tile padding not counted)
+            r.render("composite", out=img)
+            lw, lh, written = W, H, 0
+            while lw > 1 or lh > 1:
+                lw, lh = (lw + 1) // 2, (lh + 1) // 2
+                written += lw * lh
+            alg = 16 * (W * H + written)
+            peak = _measured_peak()
+            for tile in (0, 256):
+                pyr = r.pyramid(img[0], tile)
+                ms = _events_ms(lambda: r.pyramid(img[0], tile, out=pyr), 5)
+                res[f"pyramid_tile{tile}_ms"] = ms
+                res[f"pyramid_tile{tile}_gbs"] = alg / (ms / 1e3) / 1e9
+                res[f"pyramid_tile{tile}_frac_of_measured_hbm"] = alg / (ms / 1e3) / 1e9 / peak
+                del pyr
+            res["pyramid_algorithmic_bytes"] = alg
         out[f"{W}x{H}"] = res
         del img
     r.close()
@@ -663,6 +689,27 @@ def run_profile(a):
 
     import paper_1012_2909_gb300 as vr
     import synth
+
+    if a.profile == "pyramid":
+        # pyramid of a seeded 8000 x 8000 premultiplied image (the size of the paper-scale
+        # static render), row-major levels, warm-up passes then timed passes
+        g = torch.Generator(device="cuda").manual_seed(8000)
+        img = torch.rand((8000, 8000, 4), device="cuda", generator=g)
+        r = vr.Renderer(0)
+        out = r.pyramid(img)
+        for _ in range(a.warmup):
+            r.pyramid(img, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(a.steps):
+            r.pyramid(img, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "pyramid", "image": [8000, 8000],
+                          "ms_per_pyramid": e0.elapsed_time(e1) / max(a.steps, 1)}))
+        r.close()
+        return
 
     cfg = synth.CONFIGS[WORKLOAD]
     p = dict(cfg["cube"])

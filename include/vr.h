@@ -331,6 +331,27 @@ vr_status vr_load_cube_streamed(vr_ctx* ctx, vr_region_fn fn, void* user, int64_
 vr_status vr_get_stream_stats(const vr_ctx* ctx, vr_stream_stats* out);
 vr_status vr_set_stream_timeout(vr_ctx* ctx, double seconds);
 
+/*
+ * Image pyramid of a render, for viewers that show a high-resolution static
+ * render (Sec. 3) at several zoom levels, cut into tiles.  rgba (DEVICE,
+ * height x width x 4 float32, premultiplied RGBA such as an image of
+ * vr_render, 16-byte aligned) is level 0.  Level l+1 is ceil(W_l/2) x
+ * ceil(H_l/2) and its pixel (x, y) is the mean of the pixels (2x+i, 2y+j),
+ * i, j in {0, 1}, of level l that lie inside level l (one, two or four).
+ * out (DEVICE, 16-byte aligned) receives levels 1 .. L-1 one after the other,
+ * down to 1 x 1, 4 floats a pixel; each level row-major (tile = 0) or as
+ * ceil(W/tile) x ceil(H/tile) tiles of tile x tile pixels (tile a power of two
+ * in [8, 4096]), tiles row-major and pixels row-major inside a tile, with
+ * zeros where an edge tile passes the level.  Stream-ordered on `stream`.
+ * vr_pyramid_layout returns L (levels counting level 0) and the number of
+ * floats out must hold (0 for a 1 x 1 image); either pointer may be NULL.
+ * Errors: VR_ERR_INVALID_ARG for non-positive sizes, a bad tile, NULL or
+ * misaligned images.  The paper's file formats are not written here.
+ */
+vr_status vr_pyramid_layout(int32_t width, int32_t height, int32_t tile, int32_t* levels, int64_t* floats);
+vr_status vr_image_pyramid(vr_ctx* ctx, const float* rgba, int32_t width, int32_t height, int32_t tile,
+                           float* out, void* stream);
+
 /* Layout of the loaded cube; VR_ERR_STATE if none is loaded. */
 vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info);
 

@@ -102,6 +102,9 @@ SIGNATURES = {
     "vr_set_kernel_events": (ctypes.c_int, [_P, _P, _P]),
     "vr_render_mip_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "vr_get_cube_info": (ctypes.c_int, [_P, _P]),
+    "vr_pyramid_layout": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
+    "vr_image_pyramid": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "vr_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -234,6 +237,24 @@ def vr_render_mip_noalloc(ctx, out_rgba, out_max=None, stream=None, device: int 
     _check(ctx, st, "vr_render_mip_noalloc")
 
 
+def vr_pyramid_layout(width: int, height: int, tile: int = 0):
+    """(levels counting level 0, floats the packed levels 1.. take)."""
+    lv, nf = ctypes.c_int32(0), ctypes.c_int64(0)
+    _check(None, load_library().vr_pyramid_layout(width, height, tile, ctypes.byref(lv), ctypes.byref(nf)),
+           "vr_pyramid_layout")
+    return lv.value, nf.value
+
+
+def vr_image_pyramid(ctx, rgba, out, tile: int = 0, stream=None, device: int = 0):
+    """Levels 1.. of the premultiplied RGBA image rgba (device tensor, height x width x 4
+    float32) into out (device tensor of vr_pyramid_layout floats); see include/vr.h."""
+    h, w = int(rgba.shape[-3]), int(rgba.shape[-2])
+    lib = load_library()
+    st = lib.vr_image_pyramid(ctx, ctypes.c_void_p(rgba.data_ptr()), w, h, tile,
+                              ctypes.c_void_p(out.data_ptr()), _stream_handle(stream, device))
+    _check(ctx, st, "vr_image_pyramid")
+
+
 def vr_get_tuning(ctx) -> dict:
     t = vr_tuning()
     _check(ctx, load_library().vr_get_tuning(ctx, ctypes.byref(t)), "vr_get_tuning")
@@ -351,6 +372,16 @@ class Renderer:
 
     def set_path(self, path="auto"):
         vr_set_path(self.ctx, path)
+
+    def pyramid(self, rgba, tile: int = 0, out=None, stream=None):
+        """Packed levels 1.. of an image (height x width x 4) of this renderer's device."""
+        import torch
+        rgba = rgba.contiguous()
+        _, nf = vr_pyramid_layout(int(rgba.shape[-2]), int(rgba.shape[-3]), tile)
+        if out is None:
+            out = torch.empty(max(nf, 4), dtype=torch.float32, device=self.torch_device)
+        vr_image_pyramid(self.ctx, rgba, out, tile, stream, self.device)
+        return out[:nf]
 
     def cube_info(self):
         return vr_get_cube_info(self.ctx)

@@ -1541,6 +1541,43 @@ vr_status vr_render_backward(vr_ctx* ctx, vr_mode mode, const float* dL_dimg, fl
     return VR_OK;
 }
 
+namespace {
+int tile_log2(int32_t tile) {
+    if (tile == 0) return -1;
+    if (tile < 8 || tile > 4096 || (tile & (tile - 1))) return -2;
+    int l = 0;
+    while ((1 << l) < tile) ++l;
+    return l;
+}
+}  // namespace
+
+vr_status vr_pyramid_layout(int32_t width, int32_t height, int32_t tile, int32_t* levels, int64_t* floats) {
+    const int tl = tile_log2(tile);
+    if (width <= 0 || height <= 0 || tl == -2) return VR_ERR_INVALID_ARG;
+    std::vector<int> ws, hs;
+    std::vector<long long> offs;
+    const long long n = pyramid_levels(width, height, tl, ws, hs, offs);
+    if (levels) *levels = (int32_t)ws.size() + 1;
+    if (floats) *floats = 4 * n;
+    return VR_OK;
+}
+
+vr_status vr_image_pyramid(vr_ctx* ctx, const float* rgba, int32_t width, int32_t height, int32_t tile,
+                           float* out, void* stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    const int tl = tile_log2(tile);
+    if (!rgba || !out || width <= 0 || height <= 0 || tl == -2)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_image_pyramid: need images, positive sizes and tile 0 or a "
+                                             "power of two in [8, 4096]");
+    if ((reinterpret_cast<uintptr_t>(rgba) | reinterpret_cast<uintptr_t>(out)) & 15)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_image_pyramid: images must be 16-byte aligned");
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VR_CK(launch_pyramid(reinterpret_cast<const float4*>(rgba), width, height, tl, reinterpret_cast<float4*>(out), s),
+          "vr_image_pyramid: launch");
+    return VR_OK;
+}
+
 const char* vr_last_error(const vr_ctx* ctx) {
     if (!ctx) return "no context";
     return ctx->err.c_str();

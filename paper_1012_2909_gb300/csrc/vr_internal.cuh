@@ -188,6 +188,10 @@ cudaError_t launch_repack_region(const float* src, int rx0, int ry0, int rz0, in
                                  int by, int bz, const VolDev& v, vr_dtype dt, void* slot, cudaStream_t s);
 cudaError_t launch_bricks_open(const BrickFoot* foot, const int* list, int n, const float4* state, int width,
                                float ert, int* flags, cudaStream_t s);
+// Image pyramid (vr_pyramid.cu): level sizes/offsets (float4 units) and the passes.
+long long pyramid_levels(int w, int h, int tlog2, std::vector<int>& ws, std::vector<int>& hs,
+                         std::vector<long long>& offs);
+cudaError_t launch_pyramid(const float4* in, int w, int h, int tlog2, float4* out, cudaStream_t s);
 int adjoint_threads();
 int adjoint_blocks_per_sm(vr_dtype dt, int mode, int ntf);
 cudaError_t launch_adjoint(const AdjParams& p, vr_dtype dt, int grid, cudaStream_t s);

@@ -59,3 +59,17 @@ def test_abi_struct_layouts():
     assert ctypes.sizeof(vr.vr_camera) == 8 + 12 * 8 + 4 * 8 + 8
     assert ctypes.sizeof(vr.vr_options) == 24
     assert ctypes.sizeof(vr.vr_cube_info) == 3 * 8 + 6 * 4 + 2 * 8
+
+
+def test_pyramid_layout_matches_the_oracle():
+    """vr_pyramid_layout is host arithmetic: level count and buffer size for every layout."""
+    import numpy as np
+    import oracle
+    import paper_1012_2909_gb300 as vr
+    for w, h in ((1, 1), (7, 1), (1, 5), (5, 3), (64, 64), (100, 37), (1000, 999)):
+        for tile in (0, 8, 64):
+            levels, packed = oracle.pyramid(np.zeros((h, w, 4), np.float32), tile)
+            assert vr.vr_pyramid_layout(w, h, tile) == (levels, packed.size)
+    for bad in ((0, 5, 0), (5, 0, 0), (4, 4, 12), (4, 4, 4), (4, 4, 8192)):
+        with pytest.raises(vr.VrError):
+            vr.vr_pyramid_layout(*bad)
