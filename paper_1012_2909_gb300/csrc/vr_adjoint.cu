@@ -6,19 +6,20 @@
 //     C = sum_k T_k a_k c_k,   A = 1 - prod_k (1 - a_k)
 //     dC/dc_k = T_k a_k,  dC/da_k = T_k (c_k - R_k),  dA/da_k = T_k P_k
 // with R_k the colour composited behind sample k starting from transmittance 1
-// and P_k the transmittance behind it, both accumulated back to front
-// (R <- a c + (1 - a) R, P <- (1 - a) P), so nothing divides by 1 - a.
-// The forward march is recomputed segment by segment instead of storing
-// samples: the first pass keeps (first sample, T) of every segment (<= 32
-// samples inside one brick); the reverse pass re-runs each segment forward from
-// its checkpoint, keeps its values and transmittances, then sweeps it back to
-// front.  Table gradients go to per-warp FP32 copies in shared memory, then to
+// and P_k the transmittance behind it: (R_k, P_k) is the "over" composite of
+// the samples after k, an associative product, so nothing divides by 1 - a.
+// The forward march is recomputed chunk by chunk instead of storing samples:
+// the first pass keeps the transmittance at the start of every 32-sample chunk;
+// the reverse pass recomputes each chunk from its checkpoint, one sample per
+// lane, and gets (R_k, P_k) from a warp suffix scan carried from the chunks
+// behind.  Table gradients go to per-warp FP32 copies in shared memory, then to
 // per-block partials that a final kernel sums in FP64; voxel gradients are
 // scattered through the trilinear weights with FP32 atomics.
 // MIP: the image is TF(max v); the gradient reaches the first maximal sample.
 #include <algorithm>
 
 #include "vr_device.cuh"
+#include "vr_ff.cuh"
 #include "vr_tma.cuh"
 
 namespace vr {
@@ -26,8 +27,8 @@ namespace vr {
 namespace {
 
 constexpr int kAdjThreads = 128;
-constexpr int kAdjSeg = 32;       // samples per checkpoint segment (at most)
-constexpr int kAdjMaxSegs = 320;  // checkpoints per ray
+constexpr int kAdjWarps = kAdjThreads / 32;
+constexpr int kAdjMaxChunks = 320;  // 32-sample transmittance checkpoints per ray
 constexpr int kDevTooManySegments = 2;
 
 struct TFGrad {
@@ -74,186 +75,302 @@ __device__ __forceinline__ void scatter_voxels(float* __restrict__ dvol, const V
     }
 }
 
-__device__ __forceinline__ void add_tf(float* __restrict__ g, const TFGrad& t, float4 gc) {
+// g: one warp's table gradient, channel-major (g[c * n + i]), so that the lanes
+// of one atomic instruction fall on banks by table entry, not by entry mod 8.
+__device__ __forceinline__ void add_tf(float* __restrict__ g, int n, const TFGrad& t, float4 gc) {
     const float w1 = t.w, w0 = 1.f - t.w;
-    float* a = g + 4 * t.i;
-    atomicAdd(a + 0, w0 * gc.x);
-    atomicAdd(a + 1, w0 * gc.y);
-    atomicAdd(a + 2, w0 * gc.z);
-    atomicAdd(a + 3, w0 * gc.w);
-    atomicAdd(a + 4, w1 * gc.x);
-    atomicAdd(a + 5, w1 * gc.y);
-    atomicAdd(a + 6, w1 * gc.z);
-    atomicAdd(a + 7, w1 * gc.w);
+    float* a = g + t.i;
+    atomicAdd(a, w0 * gc.x);
+    atomicAdd(a + n, w0 * gc.y);
+    atomicAdd(a + 2 * n, w0 * gc.z);
+    atomicAdd(a + 3 * n, w0 * gc.w);
+    atomicAdd(a + 1, w1 * gc.x);
+    atomicAdd(a + n + 1, w1 * gc.y);
+    atomicAdd(a + 2 * n + 1, w1 * gc.z);
+    atomicAdd(a + 3 * n + 1, w1 * gc.w);
 }
 
-__device__ __forceinline__ void brick_of(const Ray& r, int k, const VolDev& v, int& bx, int& by, int& bz) {
-    const double px = fma((double)k, r.e[0], r.o[0]);
-    const double py = fma((double)k, r.e[1], r.o[1]);
-    const double pz = fma((double)k, r.e[2], r.o[2]);
-    bx = min(max(((int)floor(px)) >> v.log2B, 0), v.nbx - 1);
-    by = min(max(((int)floor(py)) >> v.log2B, 0), v.nby - 1);
-    bz = min(max(((int)floor(pz)) >> v.log2B, 0), v.nbz - 1);
+// One warp per ray, its lanes on 32 consecutive samples (a chunk).  A warp
+// claims a tile of 32 pixels, sets up their rays once (one lane each, FP64)
+// into shared memory and then walks them.  Composite: the forward pass keeps
+// the transmittance at the start of every chunk (one float) and finds the
+// termination sample by a ballot on a warp prefix product of (1 - a); the
+// reverse pass recomputes each chunk from its checkpoint and gets the colour
+// and transmittance behind every sample from a warp suffix scan of "over",
+// carried from chunk to chunk.  MIP: a warp maximum per chunk keeps the first
+// maximal sample.  Sample positions: the FP64 ray split into float-float pairs
+// once, one float-float anchor per chunk, lane offsets in FP32, each lane
+// reading the brick that holds its sample (the ghost layer makes any brick
+// within half a voxel give the same value).
+struct RaySetup {
+    float o_hi[3], o_lo[3], e_hi[3], e_lo[3];
+    int k0, k1;
+    float4 g;  // dL/dI of the pixel
+};
+
+__device__ __forceinline__ unsigned int ord_enc_f(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Brick (bx, by, bz) and slot coordinate g of sample k + lane of the ray.
+struct LaneSample {
+    int bx, by, bz;
+    float gx, gy, gz;
+    long long base;
+};
+
+// brick index along one axis of the float-float position p (clamped to the grid)
+// and the slot coordinate of p in it
+__device__ __forceinline__ int anchor_axis(ff p, const VolDev& v, int nb, float& g) {
+    const int b = min(max(((int)floorf(p.hi)) >> v.log2B, 0), nb - 1);
+    g = __fadd_rn(__fsub_rn(p.hi, (float)(b << v.log2B)), p.lo) + 0.5f;
+    return b;
+}
+
+__device__ __forceinline__ void lane_sample(const RaySetup& r, int k, int lane, float3 e32, const VolDev& v,
+                                            LaneSample& s) {
+    const float fk = (float)k;  // exact: sample indices stay below 2^24
+    float gx, gy, gz;
+    const int bx0 = anchor_axis(ff_add(ff{r.o_hi[0], r.o_lo[0]}, ff_mul_f(ff{r.e_hi[0], r.e_lo[0]}, fk)), v, v.nbx, gx);
+    const int by0 = anchor_axis(ff_add(ff{r.o_hi[1], r.o_lo[1]}, ff_mul_f(ff{r.e_hi[1], r.e_lo[1]}, fk)), v, v.nby, gy);
+    const int bz0 = anchor_axis(ff_add(ff{r.o_hi[2], r.o_lo[2]}, ff_mul_f(ff{r.e_hi[2], r.e_lo[2]}, fk)), v, v.nbz, gz);
+    const float fl = (float)lane;
+    gx = fmaf(fl, e32.x, gx);
+    gy = fmaf(fl, e32.y, gy);
+    gz = fmaf(fl, e32.z, gz);
+    const float B = (float)v.B, invB = 1.0f / B;
+    const int bx = min(max(bx0 + (int)floorf((gx - 0.5f) * invB), 0), v.nbx - 1);
+    const int by = min(max(by0 + (int)floorf((gy - 0.5f) * invB), 0), v.nby - 1);
+    const int bz = min(max(bz0 + (int)floorf((gz - 0.5f) * invB), 0), v.nbz - 1);
+    s.gx = gx - (float)((bx - bx0) << v.log2B);
+    s.gy = gy - (float)((by - by0) << v.log2B);
+    s.gz = gz - (float)((bz - bz0) << v.log2B);
+    s.bx = bx;
+    s.by = by;
+    s.bz = bz;
+    s.base = (long long)v.table[(bz * v.nby + by) * v.nbx + bx] * v.slot_elems;
 }
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adjoint(const __grid_constant__ AdjParams P) {
-    extern __shared__ float s_grad[];  // (warps per block) x ntf x 4
+    constexpr unsigned int FULL = 0xffffffffu;
+    extern __shared__ float s_grad[];  // (warps per block) x 4 channels x ntf
     __shared__ float4 s_tf[kMaxTF];
+    __shared__ RaySetup s_ray[kAdjWarps][32];
+    __shared__ float s_ckT[kAdjWarps][kAdjMaxChunks];
     const int ntf = P.tf.n;
     for (int i = threadIdx.x; i < ntf; i += blockDim.x) s_tf[i] = P.tf.tab[i];
-    const int nw = blockDim.x / 32;
-    for (int i = threadIdx.x; i < nw * ntf * 4; i += blockDim.x) s_grad[i] = 0.f;
+    for (int i = threadIdx.x; i < kAdjWarps * ntf * 4; i += blockDim.x) s_grad[i] = 0.f;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* g_tf = s_grad + warp * ntf * 4;
+    float* ckT = s_ckT[warp];
     const int tiles_per_cam = P.tiles_x * P.tiles_y;
     const int total = tiles_per_cam * P.ncams;
     const T* __restrict__ pool = static_cast<const T*>(P.vol.pool);
     const float ert = P.ert;
-    int seg_k[kAdjMaxSegs];
-    float seg_T[kAdjMaxSegs];
 
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(P.work, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
+        item = __shfl_sync(FULL, item, 0);
         if (item >= total) break;
         const int cam = item / tiles_per_cam;
         const int tile = item - cam * tiles_per_cam;
         const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
-        const int px = tx * kTileW + (lane % kTileW);
-        const int py = ty * kTileH + (lane / kTileW);
-        if (px >= P.width || py >= P.height) continue;  // ragged edge tile
-        const long long pix = ((long long)cam * P.height + py) * P.width + px;
-        const float4 gI = P.dimg[pix];
-        if (gI.x == 0.f && gI.y == 0.f && gI.z == 0.f && gI.w == 0.f) continue;
-        Ray r;
-        if (!make_ray(P.cams[cam], px, py, P.vol, P.step, r)) continue;
-        const float3 e32 = make_float3((float)r.e[0], (float)r.e[1], (float)r.e[2]);
+        {  // this lane's ray of the tile
+            const int px = tx * kTileW + (lane % kTileW);
+            const int py = ty * kTileH + (lane / kTileW);
+            bool ok = px < P.width && py < P.height;
+            Ray r;
+            float4 gI = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok) {
+                gI = P.dimg[((long long)cam * P.height + py) * P.width + px];
+                ok = (gI.x != 0.f || gI.y != 0.f || gI.z != 0.f || gI.w != 0.f) &&
+                     make_ray(P.cams[cam], px, py, P.vol, P.step, r);
+            }
+            RaySetup& rs = s_ray[warp][lane];
+            if (ok) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    rs.o_hi[a] = (float)r.o[a];
+                    rs.o_lo[a] = (float)(r.o[a] - (double)rs.o_hi[a]);
+                    rs.e_hi[a] = (float)r.e[a];
+                    rs.e_lo[a] = (float)(r.e[a] - (double)rs.e_hi[a]);
+                }
+                rs.g = gI;
+            }
+            rs.k0 = ok ? r.k0 : 0;
+            rs.k1 = ok ? r.k1 : 0;
+        }
+        __syncwarp();
+        unsigned int pending = __ballot_sync(FULL, s_ray[warp][lane].k1 > s_ray[warp][lane].k0);
+        while (pending) {
+            const int who = __ffs(pending) - 1;
+            pending &= pending - 1;
+            const RaySetup r = s_ray[warp][who];
+            const float3 e32 = make_float3(r.e_hi[0], r.e_hi[1], r.e_hi[2]);
+            const float4 gI = r.g;
 
-        if (MODE == VR_MIP) {
-            // forward: first maximal sample
-            float m = -INFINITY;
-            int kmax = -1;
-            for (int k = r.k0; k < r.k1;) {
-                Seg s;
-                seg_begin(r, k, P.vol, e32, 128, s);
-                const T* slot = pool + s.base;
-                for (int j = 0; j < s.n; ++j) {
-                    const float fj = (float)j;
-                    const float v = fetch_trilinear<T>(slot, P.vol, fmaf(fj, e32.x, s.gx), fmaf(fj, e32.y, s.gy),
-                                                       fmaf(fj, e32.z, s.gz));
-                    if (v > m) {
-                        m = v;
-                        kmax = k + j;
+            if (MODE == VR_MIP) {
+                unsigned int best = ord_enc_f(-INFINITY);
+                float m = -INFINITY;
+                int kmax = -1;
+                for (int k = r.k0; k < r.k1; k += 32) {
+                    const bool act = k + lane < r.k1;
+                    float v = -INFINITY;
+                    if (act) {
+                        LaneSample ls;
+                        lane_sample(r, k, lane, e32, P.vol, ls);
+                        v = fetch_trilinear<T>(pool + ls.base, P.vol, ls.gx, ls.gy, ls.gz);
+                    }
+                    const unsigned int e = act ? ord_enc_f(v) : 0u;
+                    const unsigned int cmax = __reduce_max_sync(FULL, e);
+                    if (cmax > best) {  // strictly greater: the first maximal sample is kept
+                        best = cmax;
+                        const int src = __ffs(__ballot_sync(FULL, act && e == cmax)) - 1;
+                        m = __shfl_sync(FULL, v, src);
+                        kmax = k + src;
                     }
                 }
-                k += s.n;
-            }
-            if (kmax < 0) continue;
-            const TFGrad t = tf_eval(s_tf, ntf, P.tf.vmin, P.tf.inv_range, m);
-            add_tf(g_tf, t, gI);
-            if (P.dvol) {
-                Seg s;
-                seg_begin(r, kmax, P.vol, e32, 1, s);
-                int bx, by, bz;
-                brick_of(r, kmax, P.vol, bx, by, bz);
-                const float dv = gI.x * t.slope.x + gI.y * t.slope.y + gI.z * t.slope.z + gI.w * t.slope.w;
-                scatter_voxels(P.dvol, P.vol, bx, by, bz, s.gx, s.gy, s.gz, dv);
-            }
-            continue;
-        }
-
-        // ---- composite: forward with checkpoints
-        int nseg = 0, last_n = 0;
-        bool overflow = false;
-        {
-            float Tr = 1.f;
-            bool done = false;
-            for (int k = r.k0; k < r.k1 && !done;) {
-                Seg s;
-                seg_begin(r, k, P.vol, e32, kAdjSeg, s);
-                if (nseg == kAdjMaxSegs) {
-                    overflow = true;
-                    break;
+                if (kmax < 0) continue;
+                if (lane == 0) {
+                    const TFGrad t = tf_eval(s_tf, ntf, P.tf.vmin, P.tf.inv_range, m);
+                    add_tf(g_tf, ntf, t, gI);
+                    if (P.dvol) {
+                        LaneSample ls;
+                        lane_sample(r, kmax, 0, e32, P.vol, ls);
+                        const float dv = gI.x * t.slope.x + gI.y * t.slope.y + gI.z * t.slope.z + gI.w * t.slope.w;
+                        scatter_voxels(P.dvol, P.vol, ls.bx, ls.by, ls.bz, ls.gx, ls.gy, ls.gz, dv);
+                    }
                 }
-                seg_k[nseg] = k;
-                seg_T[nseg] = Tr;
-                ++nseg;
-                const T* slot = pool + s.base;
-                int j = 0;
-                for (; j < s.n; ++j) {
-                    const float fj = (float)j;
-                    const float v = fetch_trilinear<T>(slot, P.vol, fmaf(fj, e32.x, s.gx), fmaf(fj, e32.y, s.gy),
-                                                       fmaf(fj, e32.z, s.gz));
-                    const float4 c = tf_lookup(s_tf, ntf, P.tf.vmin, P.tf.inv_range, v);
-                    Tr = Tr * (1.f - c.w);
-                    if (1.f - Tr >= ert) {
-                        done = true;
-                        ++j;
+                continue;
+            }
+
+            // ---- composite, forward: transmittance checkpoints per chunk, termination by ballot
+            int nch = 0, n_last = 0;
+            {
+                float Tr = 1.f;
+                bool overflow = false;
+                for (int k = r.k0; k < r.k1; k += 32) {
+                    if (nch == kAdjMaxChunks) {
+                        overflow = true;
                         break;
                     }
+                    if (lane == 0) ckT[nch] = Tr;
+                    ++nch;
+                    const int n = min(32, r.k1 - k);
+                    const bool act = lane < n;
+                    float q = 1.f;
+                    if (act) {
+                        LaneSample ls;
+                        lane_sample(r, k, lane, e32, P.vol, ls);
+                        const float v = fetch_trilinear<T>(pool + ls.base, P.vol, ls.gx, ls.gy, ls.gz);
+                        q = 1.f - tf_lookup(s_tf, ntf, P.tf.vmin, P.tf.inv_range, v).w;
+                    }
+                    float incl = q;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const float t = __shfl_up_sync(FULL, incl, off);
+                        if (lane >= off) incl *= t;
+                    }
+                    const float Tout = Tr * incl;
+                    const unsigned int done = __ballot_sync(FULL, act && 1.f - Tout >= ert);
+                    if (done) {
+                        n_last = __ffs(done);
+                        break;
+                    }
+                    n_last = n;
+                    Tr = __shfl_sync(FULL, Tout, n - 1);
                 }
-                last_n = j;
-                k += s.n;
-            }
-        }
-        if (overflow) {
-            atomicExch(P.status, kDevTooManySegments);
-            continue;
-        }
-        // ---- reverse sweep, segment by segment
-        float R0 = 0.f, R1 = 0.f, R2 = 0.f, Pt = 1.f;
-        for (int sg = nseg - 1; sg >= 0; --sg) {
-            Seg s;
-            seg_begin(r, seg_k[sg], P.vol, e32, kAdjSeg, s);
-            const int n = (sg == nseg - 1) ? last_n : s.n;
-            int bx, by, bz;
-            brick_of(r, seg_k[sg], P.vol, bx, by, bz);
-            const T* slot = pool + s.base;
-            float vb[kAdjSeg], Tb[kAdjSeg];
-            float Tr = seg_T[sg];
-#pragma unroll 1
-            for (int j = 0; j < n; ++j) {
-                const float fj = (float)j;
-                const float v = fetch_trilinear<T>(slot, P.vol, fmaf(fj, e32.x, s.gx), fmaf(fj, e32.y, s.gy),
-                                                   fmaf(fj, e32.z, s.gz));
-                vb[j] = v;
-                Tb[j] = Tr;
-                Tr = Tr * (1.f - tf_lookup(s_tf, ntf, P.tf.vmin, P.tf.inv_range, v).w);
-            }
-#pragma unroll 1
-            for (int j = n - 1; j >= 0; --j) {
-                const TFGrad t = tf_eval(s_tf, ntf, P.tf.vmin, P.tf.inv_range, vb[j]);
-                const float a = t.rgba.w, Tk = Tb[j];
-                float4 gc;
-                gc.x = gI.x * Tk * a;
-                gc.y = gI.y * Tk * a;
-                gc.z = gI.z * Tk * a;
-                gc.w = gI.w * Tk * Pt + gI.x * Tk * (t.rgba.x - R0) + gI.y * Tk * (t.rgba.y - R1) +
-                       gI.z * Tk * (t.rgba.z - R2);
-                R0 = fmaf(a, t.rgba.x, (1.f - a) * R0);
-                R1 = fmaf(a, t.rgba.y, (1.f - a) * R1);
-                R2 = fmaf(a, t.rgba.z, (1.f - a) * R2);
-                Pt *= (1.f - a);
-                add_tf(g_tf, t, gc);
-                if (P.dvol) {
-                    const float dv = gc.x * t.slope.x + gc.y * t.slope.y + gc.z * t.slope.z + gc.w * t.slope.w;
-                    const float fj = (float)j;
-                    scatter_voxels(P.dvol, P.vol, bx, by, bz, fmaf(fj, e32.x, s.gx), fmaf(fj, e32.y, s.gy),
-                                   fmaf(fj, e32.z, s.gz), dv);
+                if (overflow) {
+                    if (lane == 0) atomicExch(P.status, kDevTooManySegments);
+                    continue;
                 }
             }
+            __syncwarp();
+            // ---- reverse: chunks back to front, suffix "over" scan within a chunk
+            float Rc0 = 0.f, Rc1 = 0.f, Rc2 = 0.f, Pc = 1.f;
+            for (int c = nch - 1; c >= 0; --c) {
+                const int k = r.k0 + 32 * c;
+                const int n = c == nch - 1 ? n_last : 32;
+                const bool act = lane < n;
+                TFGrad t;
+                LaneSample ls;
+                float a = 0.f;
+                if (act) {
+                    lane_sample(r, k, lane, e32, P.vol, ls);
+                    const float v = fetch_trilinear<T>(pool + ls.base, P.vol, ls.gx, ls.gy, ls.gz);
+                    t = tf_eval(s_tf, ntf, P.tf.vmin, P.tf.inv_range, v);
+                    a = t.rgba.w;
+                }
+                const float q = 1.f - a;
+                float incl = q;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const float u = __shfl_up_sync(FULL, incl, off);
+                    if (lane >= off) incl *= u;
+                }
+                float excl = __shfl_up_sync(FULL, incl, 1);
+                if (lane == 0) excl = 1.f;
+                const float Tin = ckT[c] * excl;
+                // inclusive suffix of (A, B) = (a rgb, 1 - a) under (A1, B1) o (A2, B2) = (A1 + B1 A2, B1 B2)
+                float A0 = act ? a * t.rgba.x : 0.f, A1 = act ? a * t.rgba.y : 0.f, A2 = act ? a * t.rgba.z : 0.f;
+                float Bq = q;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const float o0 = __shfl_down_sync(FULL, A0, off), o1 = __shfl_down_sync(FULL, A1, off);
+                    const float o2 = __shfl_down_sync(FULL, A2, off), ob = __shfl_down_sync(FULL, Bq, off);
+                    if (lane + off < 32) {
+                        A0 = fmaf(Bq, o0, A0);
+                        A1 = fmaf(Bq, o1, A1);
+                        A2 = fmaf(Bq, o2, A2);
+                        Bq *= ob;
+                    }
+                }
+                // behind sample `lane`: the suffix after it, then the chunks behind this one
+                float x0 = __shfl_down_sync(FULL, A0, 1), x1 = __shfl_down_sync(FULL, A1, 1);
+                float x2 = __shfl_down_sync(FULL, A2, 1), xb = __shfl_down_sync(FULL, Bq, 1);
+                if (lane == 31) {
+                    x0 = x1 = x2 = 0.f;
+                    xb = 1.f;
+                }
+                const float R0 = fmaf(xb, Rc0, x0), R1 = fmaf(xb, Rc1, x1), R2 = fmaf(xb, Rc2, x2);
+                const float Pt = xb * Pc;
+                // carry for the chunk in front: this whole chunk over the carry
+                const float h0 = __shfl_sync(FULL, A0, 0), h1 = __shfl_sync(FULL, A1, 0);
+                const float h2 = __shfl_sync(FULL, A2, 0), hb = __shfl_sync(FULL, Bq, 0);
+                Rc0 = fmaf(hb, Rc0, h0);
+                Rc1 = fmaf(hb, Rc1, h1);
+                Rc2 = fmaf(hb, Rc2, h2);
+                Pc *= hb;
+                if (act) {
+                    float4 gc;
+                    gc.x = gI.x * Tin * a;
+                    gc.y = gI.y * Tin * a;
+                    gc.z = gI.z * Tin * a;
+                    gc.w = gI.w * Tin * Pt + gI.x * Tin * (t.rgba.x - R0) + gI.y * Tin * (t.rgba.y - R1) +
+                           gI.z * Tin * (t.rgba.z - R2);
+                    add_tf(g_tf, ntf, t, gc);
+                    if (P.dvol) {
+                        const float dv = gc.x * t.slope.x + gc.y * t.slope.y + gc.z * t.slope.z + gc.w * t.slope.w;
+                        scatter_voxels(P.dvol, P.vol, ls.bx, ls.by, ls.bz, ls.gx, ls.gy, ls.gz, dv);
+                    }
+                }
+            }
+            __syncwarp();
         }
+        __syncwarp();  // the tile's ray set-ups are read before the next tile overwrites them
     }
     __syncthreads();
     // block partial: sum of the per-warp copies
     float* out = P.tf_partials + (size_t)blockIdx.x * ntf * 4;
     for (int i = threadIdx.x; i < ntf * 4; i += blockDim.x) {
         float acc = 0.f;
-        for (int w = 0; w < nw; ++w) acc += s_grad[w * ntf * 4 + i];
+        const int e = i >> 2, c = i & 3;  // output is entry-major (ntf x 4)
+        for (int w = 0; w < kAdjWarps; ++w) acc += s_grad[w * ntf * 4 + c * ntf + e];
         out[i] = acc;
     }
 }
