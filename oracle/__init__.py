@@ -18,7 +18,8 @@ formulas, so each step is the standard definition):
 6. front-to-back "over" with termination after the sample at which
    1 - T >= ert; MIP outputs TF(max v) straight;
 7. the adjoint of 6 (reverse sweep with suffix colour / transmittance);
-8. the image pyramid of a render (2 x 2 box filter of premultiplied RGBA per level).
+8. the image pyramid of a render (2 x 2 box filter of premultiplied RGBA per level);
+9. the catalogue overlay: wireframe bounding cubes projected and drawn over a render.
 
 Parity pins: see tests/test_oracle_pins.py (closed forms for constant cubes,
 single-peak MIP, brute force along the spectral axis, sort-last invariance,
@@ -92,6 +93,8 @@ def _load():
             lib.orc_touch.argtypes = [_P, _P, _P, ctypes.c_int64, _P, ctypes.c_int]
             lib.orc_round_bf16.restype = None
             lib.orc_round_bf16.argtypes = [_P, _P, ctypes.c_int64]
+            lib.orc_overlay.restype = ctypes.c_int
+            lib.orc_overlay.argtypes = [_P, _P, ctypes.c_int64, _P, _P, _P]
             lib.orc_pyramid.restype = ctypes.c_int
             lib.orc_pyramid.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P,
                                         ctypes.POINTER(ctypes.c_int64)]
@@ -256,6 +259,24 @@ def pyramid(img: np.ndarray, tile: int = 0):
     out = np.zeros(n.value, np.float64)
     lib.orc_pyramid(_ptr(a), w, h, int(tile), _ptr(out), ctypes.byref(n))
     return levels, out
+
+
+def overlay(img: np.ndarray, cam: dict, boxes: np.ndarray, colours: np.ndarray):
+    """Wireframe bounding cubes (nbox, 6: x0 y0 z0 x1 y1 z1) drawn over the premultiplied
+    image (H, W, 4) of camera cam, box i in straight colour colours[i]; a pixel covered by
+    several boxes takes the highest index.  Returns (image float64, key int32 (H, W):
+    index + 1 of the box drawn at each pixel, 0 = none)."""
+    out = np.ascontiguousarray(img, dtype=np.float64).copy()
+    h, w = out.shape[:2]
+    assert (h, w) == (cam["height"], cam["width"])
+    bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 6)
+    col = np.ascontiguousarray(colours, dtype=np.float32).reshape(-1, 4)
+    assert len(col) == len(bx)
+    key = np.zeros((h, w), np.int32)
+    c = camera_struct(cam)
+    if _load().orc_overlay(ctypes.byref(c), _ptr(bx), len(bx), _ptr(col), _ptr(out), _ptr(key)):
+        raise ValueError("orc_overlay: bad arguments")
+    return out, key
 
 
 def pyramid_sizes(w: int, h: int):

@@ -764,3 +764,151 @@ int orc_pyramid(const float* img, int64_t w, int64_t h, int64_t tile, double* ou
     free(prev);
     return levels;
 }
+
+/* -------------------------------------------------------- catalogue overlay */
+/*
+ * Wireframe bounding cubes of a source catalogue over a render (Sec. 2: a
+ * source finder's detections, given as bounding cubes, are superimposed as
+ * wireframe boxes on the volume rendering, one colour per catalogue).
+ *
+ * Each of the 12 edges of a box is projected through the camera's inverse
+ * mapping: for the basis M = [right | up | fwd] (columns) and q = p - eye,
+ * (a, b, c) = M^-1 q; a perspective camera gives window coordinates
+ * (u, v) = (a / c, b / c) (the part of an edge with c < 1e-3 is clipped
+ * away), an orthographic one (u, v) = (a, b).  Continuous pixel coordinates
+ * are X = (u - l) W / (r - l) - 1/2, Y = (t - v) H / (t - b) - 1/2 (pixel
+ * centres at integers).  The 2-D segment is clipped to [-1, W] x [-1, H]
+ * (Liang-Barsky) and walked with n + 1 evenly spaced points, n =
+ * max(1, ceil(max(|dX|, |dY|))), each marking pixel (floor(X + 1/2),
+ * floor(Y + 1/2)) when it lies in the image.  A pixel keeps the highest box
+ * index that marks it; its premultiplied colour C, alpha A then become
+ * a c + (1 - a) C, a + (1 - a) A with the box's straight colour (c, a).
+ * All arithmetic is double precision, one rounding per operation, in the
+ * order written here.
+ */
+static void basis_inverse(const double R[3], const double U[3], const double F[3], double inv[9])
+{
+    /* m[i][j]: column 0 = right, 1 = up, 2 = fwd */
+    double m00 = R[0], m01 = U[0], m02 = F[0];
+    double m10 = R[1], m11 = U[1], m12 = F[1];
+    double m20 = R[2], m21 = U[2], m22 = F[2];
+    double c0 = m11 * m22 - m12 * m21;
+    double c1 = m12 * m20 - m10 * m22;
+    double c2 = m10 * m21 - m11 * m20;
+    double det = m00 * c0 + m01 * c1 + m02 * c2;
+    inv[0] = c0 / det;
+    inv[1] = (m02 * m21 - m01 * m22) / det;
+    inv[2] = (m01 * m12 - m02 * m11) / det;
+    inv[3] = c1 / det;
+    inv[4] = (m00 * m22 - m02 * m20) / det;
+    inv[5] = (m02 * m10 - m00 * m12) / det;
+    inv[6] = c2 / det;
+    inv[7] = (m01 * m20 - m00 * m21) / det;
+    inv[8] = (m00 * m11 - m01 * m10) / det;
+}
+
+static void cam_coords(const double inv[9], const double eye[3], const double p[3], double out[3])
+{
+    double q0 = p[0] - eye[0], q1 = p[1] - eye[1], q2 = p[2] - eye[2];
+    out[0] = inv[0] * q0 + inv[1] * q1 + inv[2] * q2;
+    out[1] = inv[3] * q0 + inv[4] * q1 + inv[5] * q2;
+    out[2] = inv[6] * q0 + inv[7] * q1 + inv[8] * q2;
+}
+
+/* Liang-Barsky: clip s in [*s0, *s1] of x0 + s dx to lo <= x <= hi; 0 if empty */
+static int clip_axis(double x0, double dx, double lo, double hi, double* s0, double* s1)
+{
+    if (dx == 0.0) return (x0 >= lo && x0 <= hi);
+    double a = (lo - x0) / dx, b = (hi - x0) / dx;
+    if (a > b) {
+        double t = a;
+        a = b;
+        b = t;
+    }
+    if (a > *s0) *s0 = a;
+    if (b < *s1) *s1 = b;
+    return *s0 <= *s1;
+}
+
+int orc_overlay(const orc_camera* cam, const double* boxes, int64_t nbox, const float* colours,
+                double* img, int32_t* key)
+{
+    if (!cam || (nbox > 0 && (!boxes || !colours)) || !img || !key) return -1;
+    const int64_t W = cam->width, H = cam->height;
+    double inv[9];
+    basis_inverse(cam->right, cam->up, cam->fwd, inv);
+    const double l = cam->win[0], r = cam->win[1], b = cam->win[2], t = cam->win[3];
+    const double sx = (double)W / (r - l), sy = (double)H / (t - b);
+    memset(key, 0, sizeof(int32_t) * (size_t)(W * H));
+    for (int64_t bi = 0; bi < nbox; ++bi) {
+        const double* bx = boxes + 6 * bi;
+        for (int e = 0; e < 12; ++e) {
+            int axis = e / 4, rest = e % 4;
+            double p0[3], p1[3];
+            int o = 0;
+            for (int a = 0; a < 3; ++a) {
+                if (a == axis) {
+                    p0[a] = bx[a];
+                    p1[a] = bx[3 + a];
+                } else {
+                    int bit = (rest >> o) & 1;
+                    ++o;
+                    p0[a] = p1[a] = bit ? bx[3 + a] : bx[a];
+                }
+            }
+            double c0[3], c1[3];
+            cam_coords(inv, cam->eye, p0, c0);
+            cam_coords(inv, cam->eye, p1, c1);
+            double u0, v0, u1, v1;
+            if (cam->type == 1) {
+                const double nearc = 1e-3;
+                if (c0[2] < nearc && c1[2] < nearc) continue;
+                if (c0[2] < nearc || c1[2] < nearc) {
+                    double s = (nearc - c0[2]) / (c1[2] - c0[2]);
+                    double* lo = c0[2] < nearc ? c0 : c1;
+                    double m0 = c0[0] + s * (c1[0] - c0[0]);
+                    double m1 = c0[1] + s * (c1[1] - c0[1]);
+                    lo[0] = m0;
+                    lo[1] = m1;
+                    lo[2] = nearc;
+                }
+                u0 = c0[0] / c0[2];
+                v0 = c0[1] / c0[2];
+                u1 = c1[0] / c1[2];
+                v1 = c1[1] / c1[2];
+            } else {
+                u0 = c0[0];
+                v0 = c0[1];
+                u1 = c1[0];
+                v1 = c1[1];
+            }
+            double X0 = (u0 - l) * sx - 0.5, Y0 = (t - v0) * sy - 0.5;
+            double X1 = (u1 - l) * sx - 0.5, Y1 = (t - v1) * sy - 0.5;
+            double dX = X1 - X0, dY = Y1 - Y0, s0 = 0.0, s1 = 1.0;
+            if (!clip_axis(X0, dX, -1.0, (double)W, &s0, &s1)) continue;
+            if (!clip_axis(Y0, dY, -1.0, (double)H, &s0, &s1)) continue;
+            double A0 = X0 + s0 * dX, B0 = Y0 + s0 * dY;
+            double A1 = X0 + s1 * dX, B1 = Y0 + s1 * dY;
+            double dA = A1 - A0, dB = B1 - B0;
+            double len = fabs(dA) > fabs(dB) ? fabs(dA) : fabs(dB);
+            int64_t n = (int64_t)ceil(len);
+            if (n < 1) n = 1;
+            for (int64_t i = 0; i <= n; ++i) {
+                double f = (double)i / (double)n;
+                int64_t px = (int64_t)floor(A0 + dA * f + 0.5);
+                int64_t py = (int64_t)floor(B0 + dB * f + 0.5);
+                if (px < 0 || px >= W || py < 0 || py >= H) continue;
+                int32_t k = (int32_t)(bi + 1);
+                if (key[py * W + px] < k) key[py * W + px] = k;
+            }
+        }
+    }
+    for (int64_t i = 0; i < W * H; ++i) {
+        if (!key[i]) continue;
+        const float* c = colours + 4 * (key[i] - 1);
+        double a = (double)c[3];
+        for (int ch = 0; ch < 3; ++ch) img[4 * i + ch] = a * (double)c[ch] + (1.0 - a) * img[4 * i + ch];
+        img[4 * i + 3] = a + (1.0 - a) * img[4 * i + 3];
+    }
+    return 0;
+}

@@ -173,6 +173,19 @@ def sources(p: dict) -> np.ndarray:
     return out[: p["nsrc"]]
 
 
+def catalogue(p: dict, k: float = 2.0) -> np.ndarray:
+    """Source-finder style catalogue of the cube's sources: one bounding cube per source,
+    (nsrc, 6) as x0, y0, z0, x1, y1, z1 = centre -+ k sigma (spatial sigma on x, y,
+    spectral on z), clipped to the cube [0, n]."""
+    s = sources(p)
+    c = s[:, 1:4]
+    r = np.stack([s[:, 4], s[:, 4], s[:, 5]], axis=1) * k
+    n = np.array([p["nx"], p["ny"], p["nz"]], np.float64)
+    lo = np.clip(c - r, 0.0, n)
+    hi = np.clip(c + r, 0.0, n)
+    return np.ascontiguousarray(np.concatenate([lo, hi], axis=1))
+
+
 def ripple_phase(p: dict) -> float:
     lib = _load()
     sp = _params(p)

@@ -57,6 +57,14 @@ MUTANTS = {
                                          "cur[4 * (y * lw + x) + c] = acc[c] / 4.0;"),
     "pyramid tiles transposed": ("return ((y / tile) * tx + x / tile) * tile * tile + (y % tile) * tile + (x % tile);",
                                  "return ((x / tile) * tx + y / tile) * tile * tile + (y % tile) * tile + (x % tile);"),
+    "overlay without the pixel-centre offset": ("double X0 = (u0 - l) * sx - 0.5, Y0 = (t - v0) * sy - 0.5;",
+                                                 "double X0 = (u0 - l) * sx, Y0 = (t - v0) * sy - 0.5;"),
+    "overlay keeps the first box": ("if (key[py * W + px] < k) key[py * W + px] = k;",
+                                    "if (key[py * W + px] == 0) key[py * W + px] = k;"),
+    "overlay blend without transmittance": (
+        "img[4 * i + ch] = a * (double)c[ch] + (1.0 - a) * img[4 * i + ch];",
+        "img[4 * i + ch] = a * (double)c[ch] + img[4 * i + ch];"),
+    "overlay perspective without the divide": ("u0 = c0[0] / c0[2];", "u0 = c0[0];"),
 }
 
 

@@ -373,3 +373,89 @@ def test_pyramid_tiled_layout():
         off_f += 4 * w * h
         off_t += 4 * tx * ty * 16
     assert off_f == flat.size and off_t == tiled.size
+
+
+# ---------------------------------------------------------------------- catalogue overlay
+def _ortho_xy(w=64, h=32):
+    # looks along +z; window = the pixel grid: pixel (px, py) centre at u = px + 1/2, v = h - py - 1/2
+    return cam(0, (0, 0, -10), (0, 0, 1), win=(0, w, 0, h), w=w, h=h)
+
+
+def _outline(x0, x1, y0, y1, w, h):
+    m = np.zeros((h, w), bool)
+    for x in range(x0, x1 + 1):
+        for y in (y0, y1):
+            if 0 <= x < w and 0 <= y < h:
+                m[y, x] = True
+    for y in range(y0, y1 + 1):
+        for x in (x0, x1):
+            if 0 <= x < w and 0 <= y < h:
+                m[y, x] = True
+    return m
+
+
+def test_overlay_axis_aligned_outline_and_blend():
+    c = _ortho_xy()
+    bg = np.tile(np.array([0.2, 0.1, 0.0, 0.5]), (32, 64, 1))
+    col = np.array([[1.0, 0.5, 0.25, 0.75]], np.float32)
+    # u = 10.5 -> pixel column 10, u = 20.5 -> 20; v = 5.5 -> row 26, v = 9.5 -> row 22
+    out, key = oracle.overlay(bg, c, np.array([[10.5, 5.5, 1.0, 20.5, 9.5, 3.0]]), col)
+    want = _outline(10, 20, 22, 26, 64, 32)
+    assert np.array_equal(key > 0, want)
+    a = 0.75
+    blend = np.array([a * 1.0 + (1 - a) * 0.2, a * 0.5 + (1 - a) * 0.1, a * 0.25, a + (1 - a) * 0.5])
+    np.testing.assert_allclose(out[want], np.tile(blend, (want.sum(), 1)), rtol=0, atol=1e-15)
+    assert np.array_equal(out[~want], bg[~want])
+
+
+def test_overlay_priority_and_clipping():
+    c = _ortho_xy()
+    boxes = np.array([[2.5, 2.5, 0, 12.5, 12.5, 1],      # box 0
+                      [8.5, 4.5, 0, 30.5, 10.5, 1],      # box 1 overlaps box 0
+                      [50.5, 20.5, 0, 80.5, 40.5, 1]])   # box 2 leaves the image
+    out, key = oracle.overlay(np.zeros((32, 64, 4)), c, boxes, np.ones((3, 4), np.float32))
+    m0 = _outline(2, 12, 19, 29, 64, 32)
+    m1 = _outline(8, 30, 21, 27, 64, 32)
+    m2 = _outline(50, 80, -9, 11, 64, 32)
+    want = np.zeros((32, 64), np.int32)
+    want[m0] = 1
+    want[m1] = 2   # a pixel of several boxes keeps the highest index
+    want[m2] = 3
+    assert np.array_equal(key, want)
+
+
+def test_overlay_perspective_against_a_pinhole_projection():
+    d, W = 40.0, 96
+    c = cam(1, (0, 0, -d), (0, 0, 1), win=(-1, 1, -1, 1), w=W, h=W)
+    box = np.array([3.0, -5.0, 2.0, 11.0, 4.0, 9.0])
+    _, key = oracle.overlay(np.zeros((W, W, 4)), c, box[None], np.ones((1, 4), np.float32))
+
+    def pix(p):  # pinhole: u = x / (z + d), v = y / (z + d); pixel centres at integers
+        u, v = p[0] / (p[2] + d), p[1] / (p[2] + d)
+        return np.array([(u + 1) / 2 * W - 0.5, (1 - v) / 2 * W - 0.5])
+
+    corners = [np.array([box[0 + 3 * i], box[1 + 3 * j], box[2 + 3 * k]])
+               for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+    for p in corners:  # every corner pixel is drawn
+        x, y = np.floor(pix(p) + 0.5).astype(int)
+        assert key[y, x] == 1
+    segs = [(pix(corners[a]), pix(corners[b])) for a in range(8) for b in range(a + 1, 8)
+            if bin(a ^ b).count("1") == 1]
+    assert len(segs) == 12
+    ys, xs = np.nonzero(key)
+    for x, y in zip(xs, ys):  # every drawn pixel is within rounding of a projected edge
+        best = min(np.linalg.norm(np.array([x, y]) - (p + np.clip(np.dot([x, y] - p, q - p) /
+                   max(np.dot(q - p, q - p), 1e-12), 0, 1) * (q - p))) for p, q in segs)
+        assert best <= 0.71
+    for p, q in segs:  # and every edge is drawn without gaps (8-connected walk)
+        n = int(np.ceil(np.abs(q - p).max())) * 4 + 1
+        for f in np.linspace(0, 1, n):
+            x, y = np.floor(p + f * (q - p) + 0.5).astype(int)
+            assert key[max(y - 1, 0):y + 2, max(x - 1, 0):x + 2].any()
+
+
+def test_overlay_box_behind_the_camera_draws_nothing():
+    c = cam(1, (0, 0, 0), (0, 0, 1), win=(-1, 1, -1, 1), w=32, h=32)
+    _, key = oracle.overlay(np.zeros((32, 32, 4)), c, np.array([[-2, -2, -9, 2, 2, -3]]),
+                            np.ones((1, 4), np.float32))
+    assert not key.any()
