@@ -329,6 +329,13 @@ def extra_hipass(dev):
                 res[f"pyramid_tile{tile}_frac_of_measured_hbm"] = alg / (ms / 1e3) / 1e9 / peak
                 del pyr
             res["pyramid_algorithmic_bytes"] = alg
+            # catalogue overlay: the sources' bounding cubes as wireframes over the render
+            import numpy as np
+            boxes = synth.catalogue(p)
+            cols = np.random.default_rng(2830).random((len(boxes), 4)).astype(np.float32)
+            r.overlay(img, boxes, cols)  # first use allocates the scratch
+            res["overlay_ms"] = _events_ms(lambda: r.overlay(img, boxes, cols), 5)
+            res["overlay_boxes"] = len(boxes)
         out[f"{W}x{H}"] = res
         del img
     r.close()

@@ -352,6 +352,30 @@ vr_status vr_pyramid_layout(int32_t width, int32_t height, int32_t tile, int32_t
 vr_status vr_image_pyramid(vr_ctx* ctx, const float* rgba, int32_t width, int32_t height, int32_t tile,
                            float* out, void* stream);
 
+/*
+ * Catalogue overlay (Sec. 2: a source finder's detections, given as bounding
+ * cubes, are superimposed as wireframe boxes on the volume rendering, one
+ * colour per catalogue).  Draws the 12 edges of every box over the images
+ * rgba (DEVICE, ncams x height x width x 4 float32, premultiplied, 16-byte
+ * aligned; modified in place) of the cameras cams (HOST, ncams cameras of one
+ * size, the ones the images were rendered with).  boxes (HOST, nbox x 6
+ * double): x0, y0, z0, x1, y1, z1 in voxel units (the cube spans [0, n]);
+ * colours (HOST, nbox x 4 float): straight RGBA of each box.
+ * An edge is projected through the camera (the inverse of the mapping in
+ * vr_camera; for a perspective camera the part closer than 1e-3 along fwd is
+ * clipped away), to continuous pixel coordinates with pixel centres at
+ * integers, clipped to the image grown by one pixel, and walked with n + 1
+ * evenly spaced points, n = max(1, ceil(max(|dx|, |dy|))), each marking the
+ * pixel it rounds to.  A marked pixel takes the colour (c, a) of the highest
+ * box index that marks it: C = a c + (1 - a) C, A = a + (1 - a) A.  Show or
+ * hide groups of boxes by what is passed.  Stream-ordered on `stream`; the
+ * host arrays may be reused when the call returns.
+ * Errors: VR_ERR_INVALID_ARG for NULL or misaligned arrays, cameras of
+ * different sizes, a bad camera type or an empty window.
+ */
+vr_status vr_overlay_boxes(vr_ctx* ctx, const vr_camera* cams, int32_t ncams, const double* boxes, int64_t nbox,
+                           const float* colours, float* rgba, void* stream);
+
 /* Layout of the loaded cube; VR_ERR_STATE if none is loaded. */
 vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info);
 

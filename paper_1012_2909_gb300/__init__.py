@@ -105,6 +105,7 @@ SIGNATURES = {
     "vr_pyramid_layout": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     "vr_image_pyramid": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "vr_overlay_boxes": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P]),
     "vr_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -255,6 +256,25 @@ def vr_image_pyramid(ctx, rgba, out, tile: int = 0, stream=None, device: int = 0
     _check(ctx, st, "vr_image_pyramid")
 
 
+def vr_overlay_boxes(ctx, cams, boxes, colours, rgba, stream=None, device: int = 0):
+    """Wireframe bounding cubes (boxes: nbox x 6 x0 y0 z0 x1 y1 z1, colours: nbox x 4 straight
+    RGBA; host arrays) drawn over the premultiplied images rgba (device tensor, ncams x H x W
+    x 4) of the cameras cams; see include/vr.h."""
+    import numpy as np
+    if isinstance(cams, dict):
+        cams = [cams]
+    arr = (vr_camera * len(cams))(*[camera_struct(c) for c in cams])
+    b = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 6)
+    c = np.ascontiguousarray(colours, dtype=np.float32).reshape(-1, 4)
+    if len(b) != len(c):
+        raise ValueError("one colour per box")
+    lib = load_library()
+    st = lib.vr_overlay_boxes(ctx, arr, len(cams), b.ctypes.data_as(ctypes.c_void_p), len(b),
+                              c.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(rgba.data_ptr()),
+                              _stream_handle(stream, device))
+    _check(ctx, st, "vr_overlay_boxes")
+
+
 def vr_get_tuning(ctx) -> dict:
     t = vr_tuning()
     _check(ctx, load_library().vr_get_tuning(ctx, ctypes.byref(t)), "vr_get_tuning")
@@ -372,6 +392,13 @@ class Renderer:
 
     def set_path(self, path="auto"):
         vr_set_path(self.ctx, path)
+
+    def overlay(self, rgba, boxes, colours, cams=None, stream=None):
+        """Draw a catalogue's bounding cubes over images rendered with this renderer's
+        cameras (or cams), in place."""
+        vr_overlay_boxes(self.ctx, self.cams if cams is None else cams, boxes, colours, rgba, stream,
+                         self.device)
+        return rgba
 
     def pyramid(self, rgba, tile: int = 0, out=None, stream=None):
         """Packed levels 1.. of an image (height x width x 4) of this renderer's device."""

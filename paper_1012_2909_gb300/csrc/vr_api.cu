@@ -73,6 +73,11 @@ struct vr_ctx {
     int work_slots = 0;
     int2* krange = nullptr;        // per-pixel sample range of the brick pass
     float4* pixdir = nullptr;      // per-pixel float-float step vector (2 x float4)
+    // catalogue overlay scratch (grown on demand)
+    int* ov_key = nullptr;
+    long long ov_key_n = 0;
+    void* ov_in = nullptr;         // cameras, boxes and colours, copied from the host
+    size_t ov_in_bytes = 0;
     unsigned int* enc = nullptr;   // per-pixel running maximum when out_max is NULL
     long long scratch_pix = 0;
     // sort-last / layered scratch
@@ -348,6 +353,8 @@ vr_status vr_destroy(vr_ctx* ctx) {
         if (ctx->work) cudaFree(ctx->work);
         if (ctx->krange) cudaFree(ctx->krange);
         if (ctx->pixdir) cudaFree(ctx->pixdir);
+        if (ctx->ov_key) cudaFree(ctx->ov_key);
+        if (ctx->ov_in) cudaFree(ctx->ov_in);
         if (ctx->enc) cudaFree(ctx->enc);
         if (ctx->tf_partials) cudaFree(ctx->tf_partials);
         for (void* p : {(void*)ctx->foot, (void*)ctx->order, (void*)ctx->tile_start, (void*)ctx->layer_buf,
@@ -1575,6 +1582,77 @@ vr_status vr_image_pyramid(vr_ctx* ctx, const float* rgba, int32_t width, int32_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VR_CK(launch_pyramid(reinterpret_cast<const float4*>(rgba), width, height, tl, reinterpret_cast<float4*>(out), s),
           "vr_image_pyramid: launch");
+    return VR_OK;
+}
+
+vr_status vr_overlay_boxes(vr_ctx* ctx, const vr_camera* cams, int32_t ncams, const double* boxes, int64_t nbox,
+                           const float* colours, float* rgba, void* stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!cams || ncams <= 0 || nbox < 0 || (nbox > 0 && (!boxes || !colours)) || !rgba)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_overlay_boxes: need cameras, boxes, colours and an image");
+    if (nbox > (1LL << 30) || ncams > 4096)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_overlay_boxes: too many boxes or cameras");
+    if (reinterpret_cast<uintptr_t>(rgba) & 15)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_overlay_boxes: the image must be 16-byte aligned");
+    const int W = cams[0].width, H = cams[0].height;
+    std::vector<OverlayCam> oc((size_t)ncams);
+    for (int i = 0; i < ncams; ++i) {
+        const vr_camera& c = cams[i];
+        if (c.width != W || c.height != H || W <= 0 || H <= 0 || (c.type != 0 && c.type != 1) ||
+            !(c.win[1] != c.win[0]) || !(c.win[3] != c.win[2]))
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_overlay_boxes: cameras need one positive size, a type "
+                                                 "and a window of positive extent");
+        OverlayCam& o = oc[(size_t)i];
+        std::memset(&o, 0, sizeof(o));
+        for (int a = 0; a < 3; ++a) {
+            o.eye[a] = c.eye[a];
+            o.right[a] = c.right[a];
+            o.up[a] = c.up[a];
+            o.fwd[a] = c.fwd[a];
+        }
+        o.l = c.win[0];
+        o.r = c.win[1];
+        o.b = c.win[2];
+        o.t = c.win[3];
+        o.type = c.type;
+        o.width = W;
+        o.height = H;
+    }
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long npix = (long long)ncams * W * H;
+    if (npix > ctx->ov_key_n) {
+        if (ctx->ov_key) cudaFree(ctx->ov_key);
+        ctx->ov_key = nullptr;
+        ctx->ov_key_n = 0;
+        VR_CK(cudaMalloc(&ctx->ov_key, sizeof(int) * (size_t)npix), "vr_overlay_boxes: scratch");
+        ctx->ov_key_n = npix;
+    }
+    // cameras, boxes and colours in one device buffer (each part 256-byte aligned)
+    auto up256 = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t cam_b = up256(sizeof(OverlayCam) * (size_t)ncams), box_b = up256(sizeof(double) * 6 * (size_t)nbox);
+    const size_t col_b = up256(sizeof(float) * 4 * (size_t)nbox);
+    const size_t need = cam_b + box_b + col_b;
+    if (need > ctx->ov_in_bytes) {
+        if (ctx->ov_in) cudaFree(ctx->ov_in);
+        ctx->ov_in = nullptr;
+        ctx->ov_in_bytes = 0;
+        VR_CK(cudaMalloc(&ctx->ov_in, need), "vr_overlay_boxes: scratch");
+        ctx->ov_in_bytes = need;
+    }
+    char* base = static_cast<char*>(ctx->ov_in);
+    VR_CK(cudaMemcpyAsync(base, oc.data(), sizeof(OverlayCam) * (size_t)ncams, cudaMemcpyHostToDevice, s),
+          "vr_overlay_boxes: copy cameras");
+    if (nbox > 0) {
+        VR_CK(cudaMemcpyAsync(base + cam_b, boxes, sizeof(double) * 6 * (size_t)nbox, cudaMemcpyHostToDevice, s),
+              "vr_overlay_boxes: copy boxes");
+        VR_CK(cudaMemcpyAsync(base + cam_b + box_b, colours, sizeof(float) * 4 * (size_t)nbox, cudaMemcpyHostToDevice,
+                              s),
+              "vr_overlay_boxes: copy colours");
+    }
+    VR_CK(launch_overlay(reinterpret_cast<const OverlayCam*>(base), ncams, reinterpret_cast<const double*>(base + cam_b),
+                         nbox, reinterpret_cast<const float*>(base + cam_b + box_b), ctx->ov_key, rgba, W, H, s),
+          "vr_overlay_boxes: launch");
     return VR_OK;
 }
 

@@ -188,6 +188,15 @@ cudaError_t launch_repack_region(const float* src, int rx0, int ry0, int rz0, in
                                  int by, int bz, const VolDev& v, vr_dtype dt, void* slot, cudaStream_t s);
 cudaError_t launch_bricks_open(const BrickFoot* foot, const int* list, int n, const float4* state, int width,
                                float ert, int* flags, cudaStream_t s);
+// Camera of the catalogue overlay: the caller's vr_camera fields, unchanged.
+struct OverlayCam {
+    double eye[3], right[3], up[3], fwd[3];
+    double l, r, b, t;
+    int type, width, height, pad;
+};
+cudaError_t launch_overlay(const OverlayCam* cams_dev, int ncams, const double* boxes, long long nbox,
+                           const float* colours, int* key, float* rgba, int width, int height, cudaStream_t s);
+
 // Image pyramid (vr_pyramid.cu): level sizes/offsets (float4 units) and the passes.
 long long pyramid_levels(int w, int h, int tlog2, std::vector<int>& ws, std::vector<int>& hs,
                          std::vector<long long>& offs);
