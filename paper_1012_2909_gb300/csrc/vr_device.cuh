@@ -64,12 +64,74 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, const 
     // a sample range is treated as ambiguous.
     const double inv_len = 1.0 / sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
     const double n[3] = {(double)v.nx, (double)v.ny, (double)v.nz};
+    double dn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        dn[a] = dd[a] * inv_len;
+        r.e[a] = dn[a] * step;
+    }
+    {
+        // The sample range from an FP32 slab test, kept only where rounding cannot
+        // change it.  With o and d rounded once from double and correctly rounded
+        // FP32 operations, each plane crossing t~ is within |t| 3 u + |o| u / |d|
+        // (u = 2^-24) of the exact one; m_a doubles that.  t_near then lies in
+        // [tnL, tnU] = [max(0, lo_a - m_a), max(0, lo_a + m_a)] and t_far in
+        // [tfL, tfU] = [min(hi_a - m_a), min(hi_a + m_a)]; an axis nearly parallel
+        // to the faces (huge t, huge m) only widens these if it can be the maximum
+        // or minimum.  The range is kept when the interval of t_near / step (and of
+        // t_far / step) holds no integer but its ceiling, else the double-precision
+        // path decides.
+        constexpr float u = 5.9604645e-8f;
+        const float fstep = (float)step;
+        float tnL = 0.f, tnU = 0.f, tfL = 3.0e38f, tfU = 3.0e38f;
+        bool clear = true, miss = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (dn[a] == 0.0) {
+                if (r.o[a] < 0.0 || r.o[a] > n[a]) miss = true;
+                continue;
+            }
+            const float o = (float)r.o[a], d = (float)dn[a];
+            if (d == 0.f) {
+                clear = false;
+                continue;
+            }
+            const float t1 = (0.f - o) / d, t2 = ((float)n[a] - o) / d;
+            const float lo_a = fminf(t1, t2), hi_a = fmaxf(t1, t2);
+            const float m = (fmaxf(fabsf(t1), fabsf(t2)) * 6.f + fabsf(o) * 2.f / fabsf(d)) * u;
+            if (!(fabsf(hi_a) + m <= 3.0e38f) || !(fabsf(lo_a) + m <= 3.0e38f)) {  // overflow: leave it to FP64
+                clear = false;
+                continue;
+            }
+            tnL = fmaxf(tnL, lo_a - m);
+            tnU = fmaxf(tnU, lo_a + m);
+            tfL = fminf(tfL, hi_a - m);
+            tfU = fminf(tfU, hi_a + m);
+        }
+        if (miss) return false;
+        if (clear && tfU < tnL) return false;  // misses the box whatever the rounding
+        if (clear && tfL > tnU && tfU < 1e9f) {
+            int k0 = 0, k1 = 0;
+            bool ok0 = tnU == 0.f;  // every face plane behind the origin: t_near = 0
+            if (!ok0 && tnL > 0.f) {
+                const float qL = tnL / fstep * (1.f - 4.f * u), qU = tnU / fstep * (1.f + 4.f * u);
+                k0 = (int)ceilf(qU);
+                ok0 = qL > (float)(k0 - 1);
+            }
+            const float qL = tfL / fstep * (1.f - 4.f * u), qU = tfU / fstep * (1.f + 4.f * u);
+            k1 = (int)ceilf(qU);
+            if (ok0 && qL > (float)(k1 - 1)) {
+                r.k0 = max(k0, 0);
+                r.k1 = k1;
+                return r.k1 > r.k0;
+            }
+        }
+    }
     double lo = 0.0, hi = 1e300;
     bool hit = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double d = dd[a] * inv_len;
-        r.e[a] = d * step;
+        const double d = dn[a];
         if (d == 0.0) {
             if (r.o[a] < 0.0 || r.o[a] > n[a]) hit = false;
         } else {
