@@ -14,6 +14,7 @@ namespace vr {
 namespace {
 
 constexpr int kSegCap = 128;  // samples between double-precision re-anchors
+constexpr int kMarchUnroll = 2;  // samples fetched together (1: 8 % slower, 4: 4 % slower)
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256)
@@ -53,24 +54,33 @@ k_march(const __grid_constant__ MarchParams P) {
                 Seg s;
                 seg_begin(r, k, P.vol, e32, kSegCap, s);
                 const T* slot = pool + s.base;
-                for (int j = 0; j < s.n; ++j) {
-                    const float fj = (float)j;
-                    const float v = fetch_trilinear<T>(slot, P.vol, fmaf(fj, e32.x, s.gx),
-                                                       fmaf(fj, e32.y, s.gy),
-                                                       fmaf(fj, e32.z, s.gz));
-                    if (MODE == VR_MIP) {
-                        m = fmaxf(m, v);
-                    } else {
-                        const float4 c = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, v);
-                        const float w = Tr * c.w;
-                        c0 = fmaf(w, c.x, c0);
-                        c1 = fmaf(w, c.y, c1);
-                        c2 = fmaf(w, c.z, c2);
-                        Tr = Tr * (1.f - c.w);
-                        if (1.f - Tr >= ert) {
-                            my_samples += (unsigned long long)(j + 1);
-                            done = true;
-                            break;
+                // kMarchUnroll samples fetched together (more loads in flight), then
+                // composited in order; a fetch past the segment repeats its last sample
+                for (int j = 0; j < s.n && !done; j += kMarchUnroll) {
+                    float v[kMarchUnroll];
+#pragma unroll
+                    for (int q = 0; q < kMarchUnroll; ++q) {
+                        const float fj = (float)min(j + q, s.n - 1);
+                        v[q] = fetch_trilinear<T>(slot, P.vol, fmaf(fj, e32.x, s.gx), fmaf(fj, e32.y, s.gy),
+                                                  fmaf(fj, e32.z, s.gz));
+                    }
+#pragma unroll
+                    for (int q = 0; q < kMarchUnroll; ++q) {
+                        if (j + q >= s.n) break;
+                        if (MODE == VR_MIP) {
+                            m = fmaxf(m, v[q]);
+                        } else {
+                            const float4 c = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, v[q]);
+                            const float w = Tr * c.w;
+                            c0 = fmaf(w, c.x, c0);
+                            c1 = fmaf(w, c.y, c1);
+                            c2 = fmaf(w, c.z, c2);
+                            Tr = Tr * (1.f - c.w);
+                            if (1.f - Tr >= ert) {
+                                my_samples += (unsigned long long)(j + q + 1);
+                                done = true;
+                                break;
+                            }
                         }
                     }
                 }
