@@ -48,7 +48,7 @@ typedef enum {
     VR_ERR_TIMEOUT = 5,     /* a bounded host wait expired                 */
     VR_ERR_IO = 6,          /* a caller-supplied data source failed        */
     VR_ERR_INTERNAL = 7,    /* a device-side check recorded an error       */
-    VR_ERR_UNSUPPORTED = 8  /* valid request this build does not implement */
+    VR_ERR_UNSUPPORTED = 8  /* a valid request the chosen path cannot serve */
 } vr_status;
 
 /* Storage type of the bricked cube.  Sampling and compositing are FP32. */
