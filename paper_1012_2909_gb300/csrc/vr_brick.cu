@@ -349,7 +349,12 @@ __global__ void k_cell_list(const __grid_constant__ BrickParams P, CellDesc* __r
 }
 
 // One chunk of camera cam's pixel rectangle of a cell -> segment records (phase 1).
-template <typename T, bool ONE>
+// Records of at most kShortRounds group rounds ("short") fill the chunk's buffer
+// from the back, the others from the front, so that the groups of a warp see
+// segments of similar length without a sorting pass.
+constexpr int kShortRounds = 3;
+
+template <typename T, bool ONE, int G>
 __device__ __forceinline__ void build_segments(const BrickParams& P, int cam_, int4 rect, float3 lo,
                                                int c0, SegRec* segs, int* cnt, int tid) {
     const int cam = ONE ? 0 : cam_;  // one camera: constant-offset parameter reads
@@ -388,7 +393,10 @@ __device__ __forceinline__ void build_segments(const BrickParams& P, int cam_, i
         const float4* pd = pd_img ? pd_img + 2 * ((long long)pyv[q] * P.width + pxv[q]) : nullptr;
         if (make_segment<T>(P, c, pxv[q], pyv[q], kr[q], lo, pd, s)) {
             s.pix += (int)(cam * img);
-            segs[atomicAdd(cnt, 1)] = s;
+            if ((s.n & 0x7fffffff) > kShortRounds * G * kUnroll)
+                segs[atomicAdd(&cnt[0], 1)] = s;
+            else
+                segs[kSegCap - 1 - atomicAdd(&cnt[1], 1)] = s;
         }
     }
 }
@@ -423,18 +431,22 @@ __device__ __forceinline__ float group_max(const T* __restrict__ tile, const Seg
 // barrier at the end of a chunk waits for at most one batch per warp.
 template <typename T, int G, int U>
 __device__ __forceinline__ void march_segments(const BrickParams& P, const T* tile, const SegRec* segs,
-                                               int nseg, int* claim, int lane) {
+                                               int nlong, int nshort, int* claim, int lane) {
     constexpr int PER_WARP = 32 / G;
     const int q = lane / G, r = lane % G;
     const unsigned int gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (q * G);
+    // batches never mix the lists: the long list is padded to whole batches
+    const int nlong_pad = (nlong + PER_WARP - 1) / PER_WARP * PER_WARP;
     for (;;) {
         int s0 = 0;
         if (lane == 0) s0 = atomicAdd(claim, PER_WARP);
         s0 = __shfl_sync(0xffffffffu, s0, 0);
-        if (s0 >= nseg) break;
-        // groups past the end of the list repeat the last record (no atomics)
-        const int si = min(s0 + q, nseg - 1);
-        const SegRec s = segs[si];
+        if (s0 >= nlong_pad + nshort) break;
+        // groups past the end of a list repeat its last record (no atomics)
+        const bool in_long = s0 < nlong_pad;
+        const int j0 = in_long ? s0 : s0 - nlong_pad, nseg = in_long ? nlong : nshort;
+        const int j = min(j0 + q, nseg - 1);
+        const SegRec s = segs[in_long ? j : kSegCap - 1 - j];
         const int n = s.n & 0x7fffffff;
         const int iters = (int)__reduce_max_sync(0xffffffffu, (unsigned int)((n + U * G - 1) / (U * G)));
         float m;
@@ -443,7 +455,7 @@ __device__ __forceinline__ void march_segments(const BrickParams& P, const T* ti
         else
             m = group_max<T, G, U, true>(tile, s, n, r, iters);
         const unsigned int e = __reduce_max_sync(gmask, ord_enc(m));
-        if (r == 0 && s0 + q < nseg) atomicMax(&P.out_enc[s.pix], e);
+        if (r == 0 && j0 + q < nseg) atomicMax(&P.out_enc[s.pix], e);
     }
 }
 
@@ -466,7 +478,7 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     __shared__ CellDesc s_desc[3];
     __shared__ int4 s_rect[3][kMaxLaunchCams];
     __shared__ int s_u[3];
-    __shared__ int s_cnt[2];
+    __shared__ int s_cnt[2][2];  // per chunk parity: long, short records
     __shared__ int s_claim[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -516,8 +528,8 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
         if (lane == 0) {
             mbar_init(&bar, 1);
             fence_mbar_init();
-            s_cnt[0] = 0;
-            s_cnt[1] = 0;
+            s_cnt[0][0] = s_cnt[0][1] = 0;
+            s_cnt[1][0] = s_cnt[1][1] = 0;
             s_claim[0] = 0;
         }
         claim(0);
@@ -533,23 +545,24 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     uint32_t phase = 0;
     next_chunk(cur, cam, c0);
     float3 lo = make_float3(s_desc[cur].lo.x, s_desc[cur].lo.y, s_desc[cur].lo.z);
-    if (cam < ncams) build_segments<T, ONE>(P, cam, s_rect[cur][cam], lo, c0, segs, &s_cnt[0], tid);
+    if (cam < ncams) build_segments<T, ONE, GROUP>(P, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[0], tid);
     bool ok = mbar_wait(&bar, phase, P.status);
     phase ^= 1u;
     if (!__syncthreads_and(ok)) return;  // no copy is in flight after a failed wait of the only load
     for (;;) {
-        const int nseg = s_cnt[chunk & 1];
+        const int nlong = s_cnt[chunk & 1][0], nshort = s_cnt[chunk & 1][1];
         if (tid == 0) {
-            s_cnt[(chunk + 1) & 1] = 0;
+            s_cnt[(chunk + 1) & 1][0] = 0;
+            s_cnt[(chunk + 1) & 1][1] = 0;
             s_claim[(chunk + 1) & 1] = 0;
         }
-        march_segments<T, GROUP, kUnroll>(P, tile, segs, nseg, &s_claim[chunk & 1], lane);
+        march_segments<T, GROUP, kUnroll>(P, tile, segs, nlong, nshort, &s_claim[chunk & 1], lane);
         __syncthreads();
         ++chunk;
         c0 += kSegCap;
         next_chunk(cur, cam, c0);
         if (cam < ncams) {  // more pixels of the same cell
-            build_segments<T, ONE>(P, cam, s_rect[cur][cam], lo, c0, segs, &s_cnt[chunk & 1], tid);
+            build_segments<T, ONE, GROUP>(P, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[chunk & 1], tid);
             __syncthreads();
             continue;
         }
@@ -561,7 +574,7 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
         c0 = 0;
         next_chunk(cur, cam, c0);
         lo = make_float3(s_desc[cur].lo.x, s_desc[cur].lo.y, s_desc[cur].lo.z);
-        if (cam < ncams) build_segments<T, ONE>(P, cam, s_rect[cur][cam], lo, c0, segs, &s_cnt[chunk & 1], tid);
+        if (cam < ncams) build_segments<T, ONE, GROUP>(P, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[chunk & 1], tid);
         // the slot after `cur` was last read two units ago: refill it now
         if (warp == 0) claim(cur == 2 ? 0 : cur + 1);
         ok = mbar_wait(&bar, phase, P.status);
