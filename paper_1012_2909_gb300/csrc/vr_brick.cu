@@ -86,6 +86,31 @@ template <> __device__ __forceinline__ float sub_wide<__nv_bfloat16>(__nv_bfloat
     return d;
 }
 
+// Two-wide FP32 operations (each lane rounds like its scalar form).  Used for
+// the pair of y-lerps of a fetch (measured: the same for position and fraction
+// was slower).
+__device__ __forceinline__ unsigned long long pk(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // Trilinear fetch from a staged cell; g in tile coordinates (lower corner
 // floor(g), 0 = ghost).  CLAMP keeps every access inside the tile; without it
 // the caller guarantees 0 <= g < extent + 1 on every axis.
@@ -107,8 +132,10 @@ __device__ __forceinline__ float tile_fetch(const T* __restrict__ t, float gx, f
     const float a1 = fmaf(fx, sub_wide<T>(t[i + SY + 1], c010), c010);
     const float a2 = fmaf(fx, sub_wide<T>(t[i + SZ + 1], c001), c001);
     const float a3 = fmaf(fx, sub_wide<T>(t[i + SZ + SY + 1], c011), c011);
-    const float b0 = fmaf(fy, a1 - a0, a0), b1 = fmaf(fy, a3 - a2, a2);
-    return fmaf(fz, b1 - b0, b0);
+    // y-lerps as one two-wide subtract and FMA: (b0, b1) = (a0, a2) + fy ((a1, a3) - (a0, a2))
+    const unsigned long long a02 = pk(a0, a2);
+    const float2 b = upk(fma2(pk(fy, fy), sub2(pk(a1, a3), a02), a02));
+    return fmaf(fz, b.y - b.x, b.x);
 }
 
 
