@@ -87,8 +87,8 @@ template <> __device__ __forceinline__ float sub_wide<__nv_bfloat16>(__nv_bfloat
 }
 
 // Two-wide FP32 operations (each lane rounds like its scalar form).  Used for
-// the pair of y-lerps of a fetch (measured: the same for position and fraction
-// was slower).
+// the pair of y-lerps of a fetch (measured: packing the x-lerps gained nothing,
+// packing position and fraction was slower).
 __device__ __forceinline__ unsigned long long pk(float a, float b) {
     unsigned long long r;
     asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
