@@ -20,14 +20,14 @@ def _relerr(g, ref):
     return float(np.max(np.abs(g - ref) / den))
 
 
-def _setup(dims, nviews, size, seed, storage="f32", ntf=64):
+def _setup(dims, nviews, size, seed, storage="f32", ntf=64, step=0.5):
     import paper_1012_2909_gb300 as vr
     p = synth.cube_params(*dims, seed=seed, nsrc=6, ripple=True, ripple_period=16.0)
     vol = synth.generate(p)
     tf = synth.viridis_ramp_tf(ntf)
     hid = synth.hidden_tf(99, ntf)
     views = synth.random_views(dims, nviews, seed=seed + 1, width=size[0], height=size[1])
-    r = vr.Renderer(0, brick=16)
+    r = vr.Renderer(0, brick=16, step=step)
     r.load_cube(vol, storage)
     r.set_camera(views)
     return vr, r, vol, tf, hid, views
@@ -35,9 +35,10 @@ def _setup(dims, nviews, size, seed, storage="f32", ntf=64):
 
 @pytest.mark.parametrize("mode", ["composite", "mip"])
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_gradients_match_oracle(mode, storage):
+@pytest.mark.parametrize("step", [0.5, 0.37])
+def test_gradients_match_oracle(mode, storage, step):
     dims = (24, 20, 28)
-    vr, r, vol, tf, hid, views = _setup(dims, 3, (24, 20), seed=31, storage=storage)
+    vr, r, vol, tf, hid, views = _setup(dims, 3, (24, 20), seed=31, storage=storage, step=step)
     # target images with the hidden table, then the L2 loss of the current table
     r.set_transfer_function(hid, -1.0, 20.0)
     target = r.render(mode).clone()
@@ -48,11 +49,11 @@ def test_gradients_match_oracle(mode, storage):
     dvol = torch.empty(vol.shape, device="cuda")
     vr.vr_render_backward(r.ctx, mode, dimg, dtf, dvol)
     torch.cuda.synchronize()
-    sc = oracle.Scene(oracle.round_storage(vol, storage), tf, -1.0, 20.0, 0.5, 0.99)
+    sc = oracle.Scene(oracle.round_storage(vol, storage), tf, -1.0, 20.0, step, 0.99)
     ref_tf, ref_vol = oracle.backward(sc, views, dimg.cpu().double().numpy(), mode)
     e_tf = _relerr(dtf.cpu().numpy(), ref_tf)
     e_vol = _relerr(dvol.cpu().numpy(), ref_vol)
-    print(mode, storage, "tf rel err", e_tf, "vol rel err", e_vol)
+    print(mode, storage, step, "tf rel err", e_tf, "vol rel err", e_vol)
     assert e_tf <= 1e-3 and e_vol <= 1e-3
     r.close()
 

@@ -89,6 +89,27 @@ def test_ragged_cube_bricks_and_tiles(vr, brick):
         assert np.all(img[3] == 0)
 
 
+@pytest.mark.parametrize("step", [0.37, 0.731, 1.3])
+def test_odd_step_sizes(vr, step):
+    """Steps whose division is inexact (the sample range comes from an FP32 slab test
+    screened by a rounding bound, with an FP64 fallback): ray-path composite and MIP and
+    the brick-path MIP, perspective, orthographic and inside-the-cube views."""
+    dims = (45, 37, 71)  # ragged against 32^3 bricks
+    p = synth.cube_params(*dims, seed=4, nsrc=8)
+    vol = synth.generate(p)
+    tf = synth.viridis_ramp_tf()
+    cams = [synth.orbit_view(dims, 23.0, 41, 29),
+            synth.ortho_view(dims, 41, 29),
+            synth.look_at(dims, (0.3, -0.2, 1.0), 41, 29, dist_factor=0.3)]  # eye inside
+    sc = oracle.Scene(vol, tf, -1.0, 20.0, step, 0.99)
+    for mode, path in (("composite", "ray"), ("mip", "ray"), ("mip", "brick")):
+        img, mx = _render(vr, vol, tf, cams, mode, brick=32, step=step, path=path)
+        for i, c in enumerate(cams):
+            st = compare(img[i].reshape(-1, 4), sc, c, mode, tol=1e-4,
+                         gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
+            assert st["nsamples"] > 0
+
+
 def test_axis_aligned_and_face_grazing_rays(vr):
     dims = (16, 12, 20)
     vol = synth.generate(synth.cube_params(*dims, seed=4, nsrc=3))
