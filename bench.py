@@ -661,7 +661,7 @@ def run_reference(a):
     sc = oracle.Scene(vol, tf, -1.0, 20.0, cfg["step"], cfg["ert"])
     rng = np.random.default_rng(3)
     W, H = cfg["image"]
-    npix = 384
+    npix = 16384  # per step: large enough that thread start-up does not dominate the oracle's time
 
     def one(i):
         cam = cams[i % len(cams)]
