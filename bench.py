@@ -138,11 +138,16 @@ def aggregate(times_ms, samples, world, device="cpu"):
 
 
 def kernel_source_hash():
+    """sha256 prefix of the brick pass's sources with comments and blank space removed, so
+    that an edit of a comment does not orphan the committed counters."""
     import hashlib
     h = hashlib.sha256()
     for f in ("vr_brick.cu", "vr_device.cuh", "vr_ff.cuh", "vr_tma.cuh"):
-        with open(os.path.join(ROOT, "paper_1012_2909_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1012_2909_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

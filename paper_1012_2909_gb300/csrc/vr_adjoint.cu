@@ -189,16 +189,16 @@ k_adjoint(const __grid_constant__ AdjParams P) {
             if (ok) {
                 gI = P.dimg[((long long)cam * P.height + py) * P.width + px];
                 ok = (gI.x != 0.f || gI.y != 0.f || gI.z != 0.f || gI.w != 0.f) &&
-                     make_ray(P.cams[cam], px, py, P.vol, P.step, r);
+                     make_ray(P.cams[cam], px, py, P.vol, ff{P.step_hi, P.step_lo}, r);
             }
             RaySetup& rs = s_ray[warp][lane];
             if (ok) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    rs.o_hi[a] = (float)r.o[a];
-                    rs.o_lo[a] = (float)(r.o[a] - (double)rs.o_hi[a]);
-                    rs.e_hi[a] = (float)r.e[a];
-                    rs.e_lo[a] = (float)(r.e[a] - (double)rs.e_hi[a]);
+                    rs.o_hi[a] = r.o[a].hi;
+                    rs.o_lo[a] = r.o[a].lo;
+                    rs.e_hi[a] = r.e[a].hi;
+                    rs.e_lo[a] = r.e[a].lo;
                 }
                 rs.g = gI;
             }

@@ -236,7 +236,8 @@ void split(double x, float& hi, float& lo) {
     lo = (float)(x - (double)hi);
 }
 
-// Float-float camera constants (see CamFF) from a double-precision camera.
+// Float-float camera constants (see CamFF) from a double-precision camera; false
+// (minv left 0, everything else filled) if the basis is singular.
 bool cam_ff(const CamDev& d, CamFF& f) {
     std::memset(&f, 0, sizeof(f));
     const double* R = d.right;
@@ -252,6 +253,13 @@ bool cam_ff(const CamDev& d, CamFF& f) {
         split(F[a] / fl, f.dir_hi[a], f.dir_lo[a]);
         f.eye[a] = (float)d.eye[a];
     }
+    f.l = (float)d.l;
+    f.t = (float)d.t;
+    f.du = (float)d.du;
+    f.dv = (float)d.dv;
+    f.type = d.type;
+    f.width = d.width;
+    f.height = d.height;
     // inverse of the column matrix M = [R U F]
     const double m[9] = {R[0], U[0], F[0], R[1], U[1], F[1], R[2], U[2], F[2]};
     const double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
@@ -263,14 +271,21 @@ bool cam_ff(const CamDev& d, CamFF& f) {
                            (m[3] * m[7] - m[4] * m[6]) / det, (m[1] * m[6] - m[0] * m[7]) / det,
                            (m[0] * m[4] - m[1] * m[3]) / det};
     for (int i = 0; i < 9; ++i) f.minv[i] = (float)inv[i];
-    f.l = (float)d.l;
-    f.t = (float)d.t;
-    f.du = (float)d.du;
-    f.dv = (float)d.dv;
-    f.type = d.type;
-    f.width = d.width;
-    f.height = d.height;
     return true;
+}
+
+// The ray constants of a camera for the paths that project nothing (image-order
+// marcher, pixel set-up, adjoint): a singular basis is fine there, minv stays 0.
+CamFF ray_cam(const CamDev& d) {
+    CamFF f;
+    cam_ff(d, f);
+    return f;
+}
+
+bool beyond(const double* v, int n, double lim) {
+    for (int i = 0; i < n; ++i)
+        if (std::fabs(v[i]) > lim) return true;
+    return false;
 }
 
 bool finite3(const double* v) {
@@ -574,6 +589,9 @@ vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams) {
             !std::isfinite(c.win[0]) || !std::isfinite(c.win[1]) || !std::isfinite(c.win[2]) ||
             !std::isfinite(c.win[3]))
             return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: non-finite camera");
+        if (beyond(c.eye, 3, 1e9) || beyond(c.right, 3, 1e9) || beyond(c.up, 3, 1e9) || beyond(c.fwd, 3, 1e9) ||
+            beyond(c.win, 4, 1e9))
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: a camera value is beyond 1e9 in magnitude");
         if (c.type == 0 && c.fwd[0] == 0.0 && c.fwd[1] == 0.0 && c.fwd[2] == 0.0)
             return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: zero forward vector");
         if (c.win[1] == c.win[0] || c.win[3] == c.win[2])
@@ -661,7 +679,7 @@ vr_status render_ray(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
     P.tile_h = ctx->tune.tile_h;
     P.tiles_x = (P.width + P.tile_w - 1) / P.tile_w;
     P.tiles_y = (P.height + P.tile_h - 1) / P.tile_h;
-    P.step = ctx->opt.step;
+    split(ctx->opt.step, P.step_hi, P.step_lo);
     P.ert = (float)ctx->opt.ert;
     P.samples = ctx->sample_counter;
     const int block = ctx->tune.block;
@@ -671,7 +689,7 @@ vr_status render_ray(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
     for (int b = 0; b < nbatch; ++b) {
         const int c0 = b * kMaxLaunchCams;
         P.ncams = std::min(kMaxLaunchCams, ncams - c0);
-        for (int i = 0; i < P.ncams; ++i) P.cams[i] = ctx->cams[(size_t)(c0 + i)];
+        for (int i = 0; i < P.ncams; ++i) P.cams[i] = ray_cam(ctx->cams[(size_t)(c0 + i)]);
         P.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)c0 * img;
         P.out_max = (mode == VR_MIP && out_max) ? out_max + (long long)c0 * img : nullptr;
         P.work = ctx->work + b;
@@ -713,13 +731,13 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
     std::memset(&pp, 0, sizeof(pp));
     pp.vol = vol_dev(ctx);
     pp.tf = tf_dev(ctx);
-    pp.step = ctx->opt.step;
+    split(ctx->opt.step, pp.step_hi, pp.step_lo);
     pp.width = W;
     pp.height = H;
     BrickParams bp;
     std::memset(&bp, 0, sizeof(bp));
     bp.vol = pp.vol;
-    bp.step = (float)ctx->opt.step;
+    split(ctx->opt.step, bp.step, bp.step_lo);
     bp.width = W;
     bp.height = H;
     int cx, cy, cz;
@@ -739,7 +757,7 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
         for (int i = 0; i < nb; ++i) {
             if (!cam_ff(ctx->cams[(size_t)(c0 + i)], bp.cams[i]))
                 return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: camera basis is singular");
-            pp.cam = ctx->cams[(size_t)(c0 + i)];
+            pp.cam = ray_cam(ctx->cams[(size_t)(c0 + i)]);
             pp.krange = ctx->krange + (long long)i * img;
             pp.pixdir = ctx->pixdir + 2 * (long long)i * img;
             pp.enc = enc + (long long)i * img;
@@ -753,7 +771,7 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
               "vr_render: brick pass");
         if (c0 + nb >= ncams && ctx->ev_stop) VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
         for (int i = 0; i < nb; ++i) {
-            pp.cam = ctx->cams[(size_t)(c0 + i)];
+            pp.cam = ray_cam(ctx->cams[(size_t)(c0 + i)]);
             pp.enc = enc + (long long)i * img;
             pp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)(c0 + i) * img;
             pp.out_max = out_max ? out_max + (long long)(c0 + i) * img : nullptr;
@@ -823,7 +841,7 @@ vr_status render_bricks_composite(vr_ctx* ctx, float* out_rgba, cudaStream_t s, 
     std::memset(&sp, 0, sizeof(sp));
     sp.vol = vol_dev(ctx);
     sp.tf = tf_dev(ctx);
-    sp.step = (float)ctx->opt.step;
+    split(ctx->opt.step, sp.step, sp.step_lo);
     sp.ert = carried ? (float)ctx->opt.ert : 2.0f;
     sp.krange = ctx->krange;
     sp.foot = ctx->foot;
@@ -835,7 +853,7 @@ vr_status render_bricks_composite(vr_ctx* ctx, float* out_rgba, cudaStream_t s, 
     std::memset(&pp, 0, sizeof(pp));
     pp.vol = sp.vol;
     pp.tf = sp.tf;
-    pp.step = ctx->opt.step;
+    split(ctx->opt.step, pp.step_hi, pp.step_lo);
     pp.width = W;
     pp.height = H;
     pp.krange = ctx->krange;
@@ -866,7 +884,7 @@ vr_status render_bricks_composite(vr_ctx* ctx, float* out_rgba, cudaStream_t s, 
         sp.layer_start = ctx->layer_buf + (L + 1);
         sp.layer_fill = ctx->layer_buf + 2 * (L + 1);
         sp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)ci * img;
-        pp.cam = cd;
+        pp.cam = ray_cam(cd);
         VR_CK(launch_pixel_setup(pp, s), "vr_render: pixel set-up");
         VR_CK(cudaMemsetAsync(sp.layer_count, 0, sizeof(int) * (size_t)L, s), "vr_render: reset");
         VR_CK(cudaMemsetAsync(sp.partial_used, 0, sizeof(unsigned long long), s), "vr_render: reset");
@@ -1079,7 +1097,7 @@ vr_status render_ooc(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
     std::memset(&sp, 0, sizeof(sp));
     sp.vol = vol_dev(ctx);
     sp.tf = tf_dev(ctx);
-    sp.step = (float)ctx->opt.step;
+    split(ctx->opt.step, sp.step, sp.step_lo);
     sp.ert = (float)ctx->opt.ert;
     sp.krange = ctx->krange;
     sp.state = ctx->state;
@@ -1087,7 +1105,7 @@ vr_status render_ooc(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
     std::memset(&pp, 0, sizeof(pp));
     pp.vol = sp.vol;
     pp.tf = sp.tf;
-    pp.step = ctx->opt.step;
+    split(ctx->opt.step, pp.step_hi, pp.step_lo);
     pp.width = W;
     pp.height = H;
     pp.krange = ctx->krange;
@@ -1095,7 +1113,7 @@ vr_status render_ooc(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
     BrickParams bp;
     std::memset(&bp, 0, sizeof(bp));
     bp.vol = sp.vol;
-    bp.step = (float)ctx->opt.step;
+    split(ctx->opt.step, bp.step, bp.step_lo);
     bp.width = W;
     bp.height = H;
     bp.ncams = 1;
@@ -1114,7 +1132,7 @@ vr_status render_ooc(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
         const CamDev& cd = ctx->cams[ci];
         st = ooc_footprints(ctx, cd, sp, order, layer_start, foot, s);
         if (st != VR_OK) return st;
-        pp.cam = cd;
+        pp.cam = ray_cam(cd);
         pp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)ci * img;
         pp.out_max = out_max ? out_max + (long long)ci * img : nullptr;
         pp.enc = (mode == VR_MIP && out_max) ? reinterpret_cast<unsigned int*>(pp.out_max) : ctx->enc;
@@ -1237,14 +1255,14 @@ vr_status brick_mip_with_scratch(vr_ctx* ctx, float* out_rgba, float* out_max, c
     std::memset(&pp, 0, sizeof(pp));
     pp.vol = vol_dev(ctx);
     pp.tf = tf_dev(ctx);
-    pp.step = ctx->opt.step;
+    split(ctx->opt.step, pp.step_hi, pp.step_lo);
     pp.width = W;
     pp.height = H;
     pp.krange = krange;
     BrickParams bp;
     std::memset(&bp, 0, sizeof(bp));
     bp.vol = pp.vol;
-    bp.step = (float)ctx->opt.step;
+    split(ctx->opt.step, bp.step, bp.step_lo);
     int cx, cy, cz;
     brick_cell_dims(ctx->dtype, &cx, &cy, &cz);
     bp.ncells_x = ctx->B / cx;
@@ -1261,7 +1279,7 @@ vr_status brick_mip_with_scratch(vr_ctx* ctx, float* out_rgba, float* out_max, c
     for (int i = 0; i < ncams; ++i) {
         if (!cam_ff(ctx->cams[(size_t)i], bp.cams[0]))
             return fail(ctx, VR_ERR_INVALID_ARG, "camera basis is singular");
-        pp.cam = ctx->cams[(size_t)i];
+        pp.cam = ray_cam(ctx->cams[(size_t)i]);
         pp.out_rgba = reinterpret_cast<float4*>(out_rgba) + (long long)i * img;
         pp.out_max = out_max ? out_max + (long long)i * img : nullptr;
         pp.enc = enc;
@@ -1529,7 +1547,7 @@ vr_status vr_render_backward(vr_ctx* ctx, vr_mode mode, const float* dL_dimg, fl
     P.mode = mode;
     P.tiles_x = (P.width + kTileW - 1) / kTileW;
     P.tiles_y = (P.height + kTileH - 1) / kTileH;
-    P.step = ctx->opt.step;
+    split(ctx->opt.step, P.step_hi, P.step_lo);
     P.ert = (float)ctx->opt.ert;
     P.dvol = dL_dvol;
     P.status = ctx->status_dev;
@@ -1537,7 +1555,7 @@ vr_status vr_render_backward(vr_ctx* ctx, vr_mode mode, const float* dL_dimg, fl
     for (int b = 0; b < nbatch; ++b) {
         const int c0 = b * kMaxLaunchCams;
         P.ncams = std::min(kMaxLaunchCams, ncams - c0);
-        for (int i = 0; i < P.ncams; ++i) P.cams[i] = ctx->cams[(size_t)(c0 + i)];
+        for (int i = 0; i < P.ncams; ++i) P.cams[i] = ray_cam(ctx->cams[(size_t)(c0 + i)]);
         P.dimg = reinterpret_cast<const float4*>(dL_dimg) + (long long)c0 * img;
         P.tf_partials = ctx->tf_partials + (size_t)b * grid * ntf * 4;
         P.work = ctx->work + b;

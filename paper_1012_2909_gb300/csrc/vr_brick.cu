@@ -2,19 +2,19 @@
 //
 // The paper decomposes a cube larger than one node's memory into pieces that
 // are rendered separately and combined (Abstract, Sec. 1).  On one GPU the
-// same decomposition streams the cube through shared memory exactly once: each
-// CTA takes a brick, stages its cells (32^3 interior voxels + a 1-voxel ghost
-// layer) with TMA into a double buffer, and marches every ray segment that
-// crosses the staged cell, one warp per segment with the lanes on consecutive
-// samples.  Partial maxima are folded with an atomic maximum, which is exact
-// and order-free, so the result equals the per-ray maximum.
+// same decomposition streams the cube through shared memory exactly once: CTAs
+// claim cells (32^3 interior voxels of a brick + a 1-voxel ghost layer), stage
+// each with one TMA copy, and march every ray segment that crosses the staged
+// cell, G lanes per segment on interleaved samples.  Partial maxima are folded
+// with an atomic maximum, which is exact and order-free, so the result equals
+// the per-ray maximum.
 //
 // Sample ownership: along each axis the cell faces are planes X; the sample
 // index where a ray crosses X is kappa(X) = (X - o)/e in FP32, the same number
 // in both cells that share the face, and monotone in X.  The intervals
 // [ceil(kappa(X_i)), ceil(kappa(X_i+1))) therefore partition the ray's samples
 // among the cells (the outermost faces are pushed to infinity), clipped to the
-// ray's [k0, k1) from the double-precision set-up.  Positions are anchored in
+// ray's [k0, k1) from the pixel set-up.  Positions are anchored in
 // float-float at the first sample of each segment and stepped in FP32.
 #include <algorithm>
 
@@ -273,7 +273,7 @@ __device__ __forceinline__ bool make_segment(const BrickParams& P, const CamFF& 
     if (ka >= kb) return false;
     // float-float anchor of sample ka
     ff E[3], O[3];
-    if (c.type == 1 && pd) {  // step vector from the pixel set-up (FP64, split)
+    if (c.type == 1 && pd) {  // step vector from the pixel set-up
         const float4 d0 = pd[0], d1 = pd[1];
         E[0] = ff{d0.x, d0.w};
         E[1] = ff{d0.y, d1.x};
@@ -291,13 +291,13 @@ __device__ __forceinline__ bool make_segment(const BrickParams& P, const CamFF& 
         const ff n2 = ff_add(ff_add(ff_mul(V[0], V[0]), ff_mul(V[1], V[1])), ff_mul(V[2], V[2]));
         const ff r = ff_rsqrt(n2);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) E[a] = ff_mul_f(ff_mul(V[a], r), P.step);
+        for (int a = 0; a < 3; ++a) E[a] = ff_mul(ff_mul(V[a], r), ff{P.step, P.step_lo});
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             O[a] = ff_add(ff_add(ff{c.base_hi[a], c.base_lo[a]}, ff_mul_f(ff{c.bx_hi[a], c.bx_lo[a]}, sx)),
                           ff_mul_f(ff{c.by_hi[a], c.by_lo[a]}, sy));
-            E[a] = ff_mul_f(ff{c.dir_hi[a], c.dir_lo[a]}, P.step);
+            E[a] = ff_mul(ff{c.dir_hi[a], c.dir_lo[a]}, ff{P.step, P.step_lo});
         }
     }
     const float fk = (float)ka;
@@ -614,18 +614,12 @@ __global__ void k_pixel_setup(const __grid_constant__ PixelParams P) {
     const int n = P.width * P.height;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         Ray r;
-        const bool hit = make_ray(P.cam, i % P.width, i / P.width, P.vol, P.step, r);
+        const bool hit = make_ray(P.cam, i % P.width, i / P.width, P.vol, ff{P.step_hi, P.step_lo}, r);
         P.krange[i] = make_int2(r.k0, r.k1);
         P.enc[i] = ord_enc(-INFINITY);
         if (hit && P.pixdir && P.cam.type == 1) {  // read only for pixels with samples
-            float h[3], l[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                h[a] = (float)r.e[a];
-                l[a] = (float)(r.e[a] - (double)h[a]);
-            }
-            P.pixdir[2 * (long long)i] = make_float4(h[0], h[1], h[2], l[0]);
-            P.pixdir[2 * (long long)i + 1] = make_float4(l[1], l[2], 0.f, 0.f);
+            P.pixdir[2 * (long long)i] = make_float4(r.e[0].hi, r.e[1].hi, r.e[2].hi, r.e[0].lo);
+            P.pixdir[2 * (long long)i + 1] = make_float4(r.e[1].lo, r.e[2].lo, 0.f, 0.f);
         }
     }
 }

@@ -2,6 +2,7 @@
 // brick-local trilinear fetch, transfer-function lookup.
 #pragma once
 
+#include "vr_ff.cuh"
 #include "vr_internal.cuh"
 
 namespace vr {
@@ -16,39 +17,49 @@ template <> __device__ __forceinline__ float ld_voxel<__nv_bfloat16>(const __nv_
     return __bfloat162float(__ldg(p));
 }
 
-// A camera ray in double precision: samples are o + k e, e = step * unit
-// direction, for k in [k0, k1).  The sample range is the half-open slab
-// interval of the box [0,nx]x[0,ny]x[0,nz] with t >= 0 (Sec. 3 renders the
-// same orientation at any output size, so everything is per pixel centre).
+// A camera ray in float-float: samples are o + k e, e = step * unit direction,
+// for k in [k0, k1).  The sample range is the half-open slab interval of the
+// box [0,nx]x[0,ny]x[0,nz] with t >= 0 (Sec. 3 renders the same orientation at
+// any output size, so everything is per pixel centre).  The few operations
+// here keep about 44 bits, so a sample up to 1e6 voxels from the origin lands
+// within 1e-7 voxel of its exact position with no double-precision arithmetic.
 struct Ray {
-    double o[3], e[3];
+    ff o[3], e[3];
     int k0, k1;
 };
 
-__device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, const VolDev& v,
-                                         double step, Ray& r) {
-    const double u = c.l + ((double)px + 0.5) * c.du;
-    const double w = c.t - ((double)py + 0.5) * c.dv;
-    double dd[3];
+// 2^-e for the binade [2^e, 2^(e+1)) holding m > 0 (2^127 for subnormal m).
+__device__ __forceinline__ float pow2_recip(float m) {
+    const int E = min((__float_as_int(m) >> 23) & 0xff, 253);
+    return __int_as_float((254 - E) << 23);
+}
+
+// Slab parameter x / d; a quotient beyond 1e30 in magnitude (a direction all
+// but parallel to the faces) is kept as +-1e30, which the axis with the
+// largest direction component never reaches, so the interval is unchanged.
+__device__ __forceinline__ ff slab_t(ff x, ff d) {
+    const float q = __fdiv_rn(x.hi, d.hi);
+    if (!(fabsf(q) < 1e30f)) return ff{copysignf(1e30f, q), 0.f};
+    return ff_div(x, d);
+}
+
+__device__ __forceinline__ bool make_ray(const CamFF& c, int px, int py, const VolDev& v, ff step, Ray& r) {
+    const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+    const bool persp = c.type == 1;
+    ff V[3];  // perspective: direction (unnormalised); orthographic: origin
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (c.type == 0) {
-            r.o[a] = c.eye[a] + u * c.right[a] + w * c.up[a];
-            dd[a] = c.fwd[a];
-        } else {
-            r.o[a] = c.eye[a];
-            dd[a] = c.fwd[a] + u * c.right[a] + w * c.up[a];
-        }
-    }
+    for (int a = 0; a < 3; ++a)
+        V[a] = ff_add(ff_add(ff{c.base_hi[a], c.base_lo[a]}, ff_mul_f(ff{c.bx_hi[a], c.bx_lo[a]}, sx)),
+                      ff_mul_f(ff{c.by_hi[a], c.by_lo[a]}, sy));
     r.k0 = r.k1 = 0;
+    const float nf[3] = {(float)v.nx, (float)v.ny, (float)v.nz};
     {
         // FP32 slab test against the box grown by one voxel: a ray that misses the
-        // grown box misses the box whatever the rounding, so it skips the FP64 work.
+        // grown box misses the box whatever the rounding, so it skips the rest.
         float lo32 = 0.f, hi32 = 3e38f;
-        const float nf[3] = {(float)v.nx, (float)v.ny, (float)v.nz};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float o = (float)r.o[a], d = (float)dd[a];
+            const float o = persp ? c.org_hi[a] : V[a].hi, d = persp ? V[a].hi : c.dir_hi[a];
             if (d == 0.f) {
                 if (o < -1.f || o > nf[a] + 1.f) return false;
             } else {
@@ -59,47 +70,57 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, const 
         }
         if (!(lo32 <= hi32 * 1.0001f + 1e-3f)) return false;
     }
-    // Reciprocals instead of divisions (double-precision division is slow on this
-    // part): t_near and t_far move by a few ulps, far inside the tolerance at which
-    // a sample range is treated as ambiguous.
-    const double inv_len = 1.0 / sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-    const double n[3] = {(double)v.nx, (double)v.ny, (double)v.nz};
-    double dn[3];
+    ff dn[3];  // unit direction
+    if (persp) {
+        // V / |V|, V first scaled by a power of two (exactly) so that |V|^2 can
+        // neither overflow nor underflow
+        const float m = fmaxf(fmaxf(fabsf(V[0].hi), fabsf(V[1].hi)), fabsf(V[2].hi));
+        if (!(m > 0.f)) return false;
+        const float sc = pow2_recip(m);
+        ff W[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        dn[a] = dd[a] * inv_len;
-        r.e[a] = dn[a] * step;
-    }
-    {
-        // The sample range from an FP32 slab test, kept only where rounding cannot
-        // change it.  With o and d rounded once from double and correctly rounded
-        // FP32 operations, each plane crossing t~ is within |t| 3 u + |o| u / |d|
-        // (u = 2^-24) of the exact one; m_a doubles that.  t_near then lies in
-        // [tnL, tnU] = [max(0, lo_a - m_a), max(0, lo_a + m_a)] and t_far in
-        // [tfL, tfU] = [min(hi_a - m_a), min(hi_a + m_a)]; an axis nearly parallel
-        // to the faces (huge t, huge m) only widens these if it can be the maximum
-        // or minimum.  The range is kept when the interval of t_near / step (and of
-        // t_far / step) holds no integer but its ceiling, else the double-precision
-        // path decides.
-        constexpr float u = 5.9604645e-8f;
-        const float fstep = (float)step;
-        float tnL = 0.f, tnU = 0.f, tfL = 3.0e38f, tfU = 3.0e38f;
-        bool clear = true, miss = false;
+        for (int a = 0; a < 3; ++a) W[a] = ff{V[a].hi * sc, V[a].lo * sc};
+        const ff rn = ff_rsqrt(ff_add(ff_add(ff_mul(W[0], W[0]), ff_mul(W[1], W[1])), ff_mul(W[2], W[2])));
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if (dn[a] == 0.0) {
-                if (r.o[a] < 0.0 || r.o[a] > n[a]) miss = true;
+            r.o[a] = ff{c.org_hi[a], c.org_lo[a]};
+            dn[a] = ff_mul(W[a], rn);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r.o[a] = V[a];
+            dn[a] = ff{c.dir_hi[a], c.dir_lo[a]};
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r.e[a] = ff_mul(dn[a], step);
+    {
+        // The sample range from an FP32 slab test, kept only where rounding cannot
+        // change it.  With o and d rounded once from their float-float values and
+        // correctly rounded FP32 operations, each plane crossing t~ is within
+        // |t| 3 u + |o| u / |d| (u = 2^-24) of the exact one; m_a doubles that.
+        // t_near then lies in [tnL, tnU] = [max(0, lo_a - m_a), max(0, lo_a + m_a)]
+        // and t_far in [tfL, tfU] = [min(hi_a - m_a), min(hi_a + m_a)]; an axis
+        // nearly parallel to the faces (huge t, huge m) only widens these if it can
+        // be the maximum or minimum.  The range is kept when the interval of
+        // t_near / step (and of t_far / step) holds no integer but its ceiling,
+        // else the float-float path decides.
+        constexpr float u = 5.9604645e-8f;
+        const float fstep = step.hi;
+        float tnL = 0.f, tnU = 0.f, tfL = 3.0e38f, tfU = 3.0e38f;
+        bool clear = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float o = r.o[a].hi, d = dn[a].hi;
+            if (d == 0.f) {  // exactly parallel (hi == 0 means the pair is 0)
+                if (o < 0.f || ff_lt(ff{nf[a], 0.f}, r.o[a])) return false;
                 continue;
             }
-            const float o = (float)r.o[a], d = (float)dn[a];
-            if (d == 0.f) {
-                clear = false;
-                continue;
-            }
-            const float t1 = (0.f - o) / d, t2 = ((float)n[a] - o) / d;
+            const float t1 = (0.f - o) / d, t2 = (nf[a] - o) / d;
             const float lo_a = fminf(t1, t2), hi_a = fmaxf(t1, t2);
             const float m = (fmaxf(fabsf(t1), fabsf(t2)) * 6.f + fabsf(o) * 2.f / fabsf(d)) * u;
-            if (!(fabsf(hi_a) + m <= 3.0e38f) || !(fabsf(lo_a) + m <= 3.0e38f)) {  // overflow: leave it to FP64
+            if (!(fabsf(hi_a) + m <= 3.0e38f) || !(fabsf(lo_a) + m <= 3.0e38f)) {  // overflow: not screened
                 clear = false;
                 continue;
             }
@@ -108,7 +129,6 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, const 
             tfL = fminf(tfL, hi_a - m);
             tfU = fminf(tfU, hi_a + m);
         }
-        if (miss) return false;
         if (clear && tfU < tnL) return false;  // misses the box whatever the rounding
         if (clear && tfL > tnU && tfU < 1e9f) {
             int k0 = 0, k1 = 0;
@@ -127,24 +147,23 @@ __device__ __forceinline__ bool make_ray(const CamDev& c, int px, int py, const 
             }
         }
     }
-    double lo = 0.0, hi = 1e300;
-    bool hit = true;
+    // float-float slab test: t = (plane - o) / d per axis, then ceil(t / step)
+    ff lo = {0.f, 0.f}, hi = {1e30f, 0.f};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double d = dn[a];
-        if (d == 0.0) {
-            if (r.o[a] < 0.0 || r.o[a] > n[a]) hit = false;
-        } else {
-            const double inv_d = 1.0 / d;
-            const double t1 = (0.0 - r.o[a]) * inv_d, t2 = (n[a] - r.o[a]) * inv_d;
-            lo = fmax(lo, fmin(t1, t2));
-            hi = fmin(hi, fmax(t1, t2));
-        }
+        if (dn[a].hi == 0.f) continue;  // inside its slab (checked above)
+        const ff t1 = slab_t(ff_neg(r.o[a]), dn[a]);
+        const ff t2 = slab_t(ff_add(ff{nf[a], 0.f}, ff_neg(r.o[a])), dn[a]);
+        const bool sw = ff_lt(t2, t1);
+        const ff tl = sw ? t2 : t1, th = sw ? t1 : t2;
+        if (ff_lt(lo, tl)) lo = tl;
+        if (ff_lt(th, hi)) hi = th;
     }
-    if (!hit || !(lo < hi)) return false;
-    const double a = ceil(lo / step), b = ceil(hi / step);
-    r.k0 = (int)fmax(a, 0.0);
-    r.k1 = (int)fmin(b, 2.0e9);
+    if (!ff_lt(lo, hi)) return false;
+    const ff qa = ff_div(lo, step), qb = ff_div(hi, step);
+    const long long kmax = 2000000000LL;
+    r.k0 = (int)(qa.hi < 2e9f ? max(ff_ceil(qa), 0LL) : kmax);
+    r.k1 = (int)(qb.hi < 2e9f ? min(ff_ceil(qb), kmax) : kmax);
     return r.k1 > r.k0;
 }
 
@@ -162,17 +181,23 @@ struct Seg {
 // stay inside its interior (at least 1, at most cap).
 __device__ __forceinline__ bool seg_begin(const Ray& r, int k, const VolDev& v, float3 e32,
                                           int cap, Seg& s) {
-    const double px = fma((double)k, r.e[0], r.o[0]);
-    const double py = fma((double)k, r.e[1], r.o[1]);
-    const double pz = fma((double)k, r.e[2], r.o[2]);
-    int bx = ((int)floor(px)) >> v.log2B, by = ((int)floor(py)) >> v.log2B,
-        bz = ((int)floor(pz)) >> v.log2B;
-    bx = min(max(bx, 0), v.nbx - 1);
-    by = min(max(by, 0), v.nby - 1);
-    bz = min(max(bz, 0), v.nbz - 1);
-    s.gx = (float)(px - (double)(bx << v.log2B)) + 0.5f;
-    s.gy = (float)(py - (double)(by << v.log2B)) + 0.5f;
-    s.gz = (float)(pz - (double)(bz << v.log2B)) + 0.5f;
+    const ff kk = ff_of_int(k);
+    const int nb[3] = {v.nbx, v.nby, v.nbz};
+    int b[3];
+    float g[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const ff p = ff_add(r.o[a], ff_mul(r.e[a], kk));
+        const int bi = min(max((int)ff_floor(p) >> v.log2B, 0), nb[a] - 1);
+        b[a] = bi;
+        // p.hi minus the brick origin is exact (both are multiples of ulp(p.hi)
+        // and the difference is no larger than p.hi or one voxel)
+        g[a] = __fadd_rn(__fsub_rn(p.hi, (float)(bi << v.log2B)), p.lo) + 0.5f;
+    }
+    const int bx = b[0], by = b[1], bz = b[2];
+    s.gx = g[0];
+    s.gy = g[1];
+    s.gz = g[2];
     const float hiB = (float)v.B + 0.5f;
     float m = (float)cap;
     if (e32.x > 0.f) m = fminf(m, (hiB - s.gx) / e32.x); else if (e32.x < 0.f) m = fminf(m, (0.5f - s.gx) / e32.x);

@@ -59,4 +59,37 @@ __device__ __forceinline__ ff ff_rsqrt(ff x) {
     return ff_quick(r, corr);
 }
 
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+
+// x / y to about 44 bits: FP32 quotient, one correction from the float-float
+// remainder x - q y.
+__device__ __forceinline__ ff ff_div(ff x, ff y) {
+    const float q = __fdiv_rn(x.hi, y.hi);
+    const ff r = ff_add(x, ff_neg(ff_mul_f(y, q)));
+    return ff_quick(q, __fdiv_rn(r.hi, y.hi));
+}
+
+__device__ __forceinline__ bool ff_lt(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+// floor and ceiling of hi + lo as integers (|hi| < 2^62).  If hi is not an
+// integer, lo cannot carry the sum across one: |lo| <= ulp(hi) / 2, and hi and
+// the integers on either side of it are all multiples of ulp(hi).
+__device__ __forceinline__ long long ff_ceil(ff x) {
+    const float c = ceilf(x.hi);
+    if (c != x.hi) return (long long)c;
+    return (long long)c + (long long)ceilf(x.lo);
+}
+
+__device__ __forceinline__ long long ff_floor(ff x) {
+    const float f = floorf(x.hi);
+    if (f != x.hi) return (long long)f;
+    return (long long)f + (long long)floorf(x.lo);
+}
+
+// An int as an exact float-float pair (|k| <= 2^31 - 128).
+__device__ __forceinline__ ff ff_of_int(int k) {
+    const float h = __int2float_rn(k);
+    return ff{h, __int2float_rn(k - __float2int_rz(h))};
+}
+
 }  // namespace vr

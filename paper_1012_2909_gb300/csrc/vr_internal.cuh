@@ -18,8 +18,8 @@ constexpr int kMaxLaunchCams = 32;   // cameras carried by value in one launch
 constexpr int kMaxTF = 1024;         // transfer-function entries
 constexpr int kTileW = 8, kTileH = 4; // pixels of one warp work item
 
-// One camera as the kernels see it (double precision; Sec. 3's off-axis
-// sub-windows are just other (l, t, du, dv)).
+// One camera as the host keeps it (double precision; Sec. 3's off-axis
+// sub-windows are just other (l, t, du, dv)); kernels get it as a CamFF.
 struct CamDev {
     double eye[3], right[3], up[3], fwd[3];
     double l, t, du, dv;  // u = l + (px + 1/2) du, v = t - (py + 1/2) dv
@@ -44,23 +44,7 @@ struct TFDev {
     float vmin, inv_range, pad;
 };
 
-struct MarchParams {
-    VolDev vol;
-    TFDev tf;
-    CamDev cams[kMaxLaunchCams];
-    int ncams, width, height, mode;
-    int tiles_x, tiles_y;
-    int tile_w, tile_h;          // pixels of one warp work item (tile_w * tile_h == 32)
-    double step;
-    float ert;
-    int pad2;
-    float4* out_rgba;            // pixels of camera 0 of this launch
-    float* out_max;              // may be null
-    unsigned long long* samples; // may be null
-    int* work;                   // zeroed work counter of this launch
-};
-
-// Float-float camera constants for the brick pass.  With sx = px + 1/2,
+// Float-float camera constants, split on the host from a CamDev.  With sx = px + 1/2,
 // sy = py + 1/2:  V = base + sx bx + sy by.  Perspective: origin org, direction
 // V / |V|.  Orthographic: origin V, direction dir (constant).  minv is the
 // inverse of the column matrix [right up fwd], used to project cell corners.
@@ -74,16 +58,34 @@ struct CamFF {
     int type, width, height, pad;
 };
 
+struct MarchParams {
+    VolDev vol;
+    TFDev tf;
+    CamFF cams[kMaxLaunchCams];
+    int ncams, width, height, mode;
+    int tiles_x, tiles_y;
+    int tile_w, tile_h;          // pixels of one warp work item (tile_w * tile_h == 32)
+    float step_hi, step_lo;      // the sample spacing as a float-float pair
+    float ert;
+    int pad2;
+    float4* out_rgba;            // pixels of camera 0 of this launch
+    float* out_max;              // may be null
+    unsigned long long* samples; // may be null
+    int* work;                   // zeroed work counter of this launch
+};
+
+
+
 // Launch parameters of the brick (object-order) pass for up to kMaxLaunchCams
 // cameras of one size; per-pixel arrays are camera-major (cam * W * H + pixel).
 struct BrickParams {
     VolDev vol;
     CamFF cams[kMaxLaunchCams];
     int ncams, width, height;
-    float step;
+    float step, step_lo;     // the sample spacing as a float-float pair
     int ncells_x, ncells_y, ncells_z;  // cells per brick along each axis
-    int nbricks;
-    const int2* krange;      // per pixel [k0, k1) from the double-precision set-up
+    int nbricks, pad_b;
+    const int2* krange;      // per pixel [k0, k1) from the pixel set-up
     const float4* pixdir;    // optional, perspective cameras: per pixel the step
                              // vector e in float-float, 2 x float4 (hi.xyz, lo.x),
                              // (lo.y, lo.z, -, -), written by the pixel set-up
@@ -98,11 +100,10 @@ struct BrickParams {
 struct AdjParams {
     VolDev vol;
     TFDev tf;
-    CamDev cams[kMaxLaunchCams];
+    CamFF cams[kMaxLaunchCams];
     int ncams, width, height, mode;
     int tiles_x, tiles_y;
-    int pad0, pad1;
-    double step;
+    float step_hi, step_lo;  // the sample spacing as a float-float pair
     float ert;
     int pad2;
     const float4* dimg;   // dL/dI of camera 0 of this launch
@@ -125,8 +126,9 @@ struct SortParams {
     VolDev vol;
     TFDev tf;
     CamFF cam;
-    float step, ert;
-    int max_layers, pad;
+    float step, step_lo;              // the sample spacing as a float-float pair
+    float ert;
+    int max_layers;
     int eye_brick[3], all_bricks;     // floor(eye / B); all_bricks: ignore residency (out of core)
     const int2* krange;
     BrickFoot* foot;                  // per brick
@@ -149,8 +151,8 @@ struct SortParams {
 struct PixelParams {
     VolDev vol;
     TFDev tf;
-    CamDev cam;
-    double step;
+    CamFF cam;
+    float step_hi, step_lo;
     int width, height;
     int2* krange;
     float4* pixdir;  // optional: per-pixel float-float step vector (see BrickParams)

@@ -13,7 +13,7 @@ namespace vr {
 
 namespace {
 
-constexpr int kSegCap = 128;  // samples between double-precision re-anchors
+constexpr int kSegCap = 128;  // samples between float-float re-anchors
 // Samples fetched together per step.  The marcher waits on its gathers, so more
 // loads in flight beat more resident warps: with the register count left free
 // (launch bound 256 x 1), 4 measured fastest (3: +2 %, 6: +2 %, 2: +9 %), and
@@ -46,12 +46,11 @@ k_march(const __grid_constant__ MarchParams P) {
         const int py = ty * P.tile_h + (lane / P.tile_w);
         if (px >= P.width || py >= P.height) continue;  // ragged edge tile; the lane
                                                         // rejoins at the next shuffle
-        const CamDev& C = P.cams[cam];
         Ray r;
-        const bool hit = make_ray(C, px, py, P.vol, P.step, r);
+        const bool hit = make_ray(P.cams[cam], px, py, P.vol, ff{P.step_hi, P.step_lo}, r);
         float c0 = 0.f, c1 = 0.f, c2 = 0.f, Tr = 1.f, m = -INFINITY;
         if (hit) {
-            const float3 e32 = make_float3((float)r.e[0], (float)r.e[1], (float)r.e[2]);
+            const float3 e32 = make_float3(r.e[0].hi, r.e[1].hi, r.e[2].hi);
             int k = r.k0;
             bool done = false;
             while (k < r.k1 && !done) {

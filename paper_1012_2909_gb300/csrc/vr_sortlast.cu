@@ -205,13 +205,13 @@ __device__ __forceinline__ bool brick_segment(const SortParams& P, int px, int p
         const ff n2 = ff_add(ff_add(ff_mul(V[0], V[0]), ff_mul(V[1], V[1])), ff_mul(V[2], V[2]));
         const ff r = ff_rsqrt(n2);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) E[a] = ff_mul_f(ff_mul(V[a], r), P.step);
+        for (int a = 0; a < 3; ++a) E[a] = ff_mul(ff_mul(V[a], r), ff{P.step, P.step_lo});
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             O[a] = ff_add(ff_add(ff{c.base_hi[a], c.base_lo[a]}, ff_mul_f(ff{c.bx_hi[a], c.bx_lo[a]}, sx)),
                           ff_mul_f(ff{c.by_hi[a], c.by_lo[a]}, sy));
-            E[a] = ff_mul_f(ff{c.dir_hi[a], c.dir_lo[a]}, P.step);
+            E[a] = ff_mul(ff{c.dir_hi[a], c.dir_lo[a]}, ff{P.step, P.step_lo});
         }
     }
     const float fk = (float)ka;

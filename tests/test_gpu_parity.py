@@ -92,7 +92,7 @@ def test_ragged_cube_bricks_and_tiles(vr, brick):
 @pytest.mark.parametrize("step", [0.37, 0.731, 1.3])
 def test_odd_step_sizes(vr, step):
     """Steps whose division is inexact (the sample range comes from an FP32 slab test
-    screened by a rounding bound, with an FP64 fallback): ray-path composite and MIP and
+    screened by a rounding bound, with a float-float fallback): ray-path composite and MIP and
     the brick-path MIP, perspective, orthographic and inside-the-cube views."""
     dims = (45, 37, 71)  # ragged against 32^3 bricks
     p = synth.cube_params(*dims, seed=4, nsrc=8)
@@ -108,6 +108,23 @@ def test_odd_step_sizes(vr, step):
             st = compare(img[i].reshape(-1, 4), sc, c, mode, tol=1e-4,
                          gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
             assert st["nsamples"] > 0
+
+
+def test_distant_narrow_view(vr):
+    """An eye ~1e5 voxels away with a 0.02 degree field of view: the FP32 screen of the
+    sample range fails for most rays, so the float-float slab test decides them, and the
+    anchors o + k e are far from the origin."""
+    dims = (45, 37, 71)
+    vol = synth.generate(synth.cube_params(*dims, seed=6, nsrc=8))
+    tf = synth.viridis_ramp_tf()
+    cam = synth.look_at(dims, (0.3, 0.2, 1.0), 41, 29, fov_deg=0.02, dist_factor=2000.0)
+    assert np.linalg.norm(np.asarray(cam["eye"])) > 5e4
+    sc = oracle.Scene(vol, tf, -1.0, 20.0, 0.5, 0.99)
+    for mode, path in (("composite", "ray"), ("mip", "ray"), ("mip", "brick")):
+        img, mx = _render(vr, vol, tf, [cam], mode, brick=32, path=path)
+        st = compare(img[0].reshape(-1, 4), sc, cam, mode, tol=1e-4,
+                     gpu_max=mx[0] if mode == "mip" else None, max_tol=2e-3)
+        assert st["nsamples"] > 0
 
 
 def test_axis_aligned_and_face_grazing_rays(vr):
@@ -213,6 +230,10 @@ def test_status_codes(vr):
     bad["type"] = 7
     with pytest.raises(vr.VrError) as e:
         r.set_camera(bad)
+    assert e.value.status == vr.VR_ERR_INVALID_ARG
+    far = dict(synth.orbit_view((8, 8, 8), 0.0, 4, 4), eye=[0.0, 0.0, -2e9])
+    with pytest.raises(vr.VrError) as e:  # beyond the float-float set-up's range
+        r.set_camera(far)
     assert e.value.status == vr.VR_ERR_INVALID_ARG
     r.close()
 
