@@ -202,6 +202,25 @@ def _events_ms(fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def path_times(r, cams, out):
+    """ms per frame of every render path on the same frames: composite through the
+    image-order marcher (ERT), sort-last partial images folded in visibility order and the
+    layered carried state (both without termination); MIP through the brick pass and the
+    marcher."""
+    res = {"frames": len(cams)}
+    for mode, paths in (("composite", ("ray", "sortlast", "layered")), ("mip", ("brick", "ray"))):
+        for path in paths:
+            r.set_path(path)
+            tot = 0.0
+            for cam in cams:
+                r.set_camera(cam)
+                r.render(mode, out=out)  # first render of a view: plans and scratch
+                tot += _events_ms(lambda: r.render(mode, out=out), 2)
+            res[f"{mode}_{path}_ms"] = tot / len(cams)
+    r.set_path("auto")
+    return res
+
+
 def extra_wall(dev):
     """5 x 5 wall of 1920 x 1080 panels (25 off-axis frusta of one camera) on the
     2048 x 2048 x 1024 FP16 cube: batched (one graph launch per mode, autotuned)
@@ -580,7 +599,9 @@ def run_ours(a):
                 float(esamples) * world / (e2e_ms / 1e3),
                 "unit": "samples/s", "h2d_bytes_per_step": 144,
                 "d2h_bytes_per_step": 2 * H * W * 4 * 4},
-        "gpu_launches": 4 * a.steps,
+        # per step: k_march (composite); k_pixel_setup, k_cell_list, k_brick_mip,
+        # k_mip_finalize (MIP)
+        "gpu_launches": 5 * a.steps,
         "clocks": clocks,
         "generation_s": gen_s,
     }
@@ -628,9 +649,12 @@ def run_ours(a):
         tot += e0.elapsed_time(e1)
     res["ms_per_frame"]["composite"] = tot / len(cams)
     if rank == 0 and not a.no_extras:
+        res["extras"] = {}
+        t0 = time.time()
+        res["extras"]["paths"] = path_times(rq, cams[::6], out_c)
+        res["extras"]["paths"]["wall_s"] = time.time() - t0
         del rq, r32
         torch.cuda.empty_cache()
-        res["extras"] = {}
         for name, fn in (("wall", extra_wall), ("hipass", extra_hipass), ("diff", extra_diff),
                          ("ooc", extra_ooc)):
             t0 = time.time()
