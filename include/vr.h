@@ -117,11 +117,17 @@ typedef struct {
 typedef struct {
     int32_t brick;  /* interior brick edge in voxels, power of two in [8, 256];
                        default 128.  Bricks carry a 1-voxel ghost layer.    */
-    int32_t pad_;
+    int32_t flags;  /* VR_OPT_* bits; default 0                            */
     double step;    /* sample spacing along the ray in voxels, > 0; default 0.5 */
     double ert;     /* early termination once accumulated alpha >= ert after a
                        sample; default 0.99; a value > 1 disables it          */
 } vr_options;
+
+/* vr_options.flags: keep one brick store only.  By default vr_load_cube also
+ * keeps a copy of the store shifted by one element along x, when it fits in
+ * half of the free device memory, so that the image-order marcher reads each
+ * pair of x-neighbours of a trilinear fetch with one aligned load. */
+#define VR_OPT_SINGLE_STORE 1
 
 typedef struct vr_ctx vr_ctx;
 
@@ -133,7 +139,8 @@ typedef struct {
     int32_t pitch;           /* x pitch of a stored brick row, elements   */
     int32_t dtype;           /* vr_dtype                                  */
     int64_t brick_bytes;     /* bytes of one stored brick slot            */
-    int64_t store_bytes;     /* bytes of the whole brick store            */
+    int64_t store_bytes;     /* bytes of the whole brick store, with its
+                                x-shifted copy when one is kept           */
 } vr_cube_info;
 
 /* Fill *opt with the defaults (brick 128, step 0.5, ert 0.99). */

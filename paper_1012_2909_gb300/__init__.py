@@ -28,6 +28,7 @@ VR_F32, VR_F16, VR_BF16 = 0, 1, 2
 VR_COMPOSITE, VR_MIP = 0, 1
 DTYPES = {"f32": VR_F32, "f16": VR_F16, "bf16": VR_BF16}
 MODES = {"composite": VR_COMPOSITE, "mip": VR_MIP}
+VR_OPT_SINGLE_STORE = 1
 VR_PATH_AUTO, VR_PATH_RAY, VR_PATH_BRICK, VR_PATH_SORTLAST, VR_PATH_LAYERED = 0, 1, 2, 3, 4
 PATHS = {"auto": VR_PATH_AUTO, "ray": VR_PATH_RAY, "brick": VR_PATH_BRICK, "sortlast": VR_PATH_SORTLAST,
          "layered": VR_PATH_LAYERED}
@@ -48,7 +49,7 @@ class vr_camera(ctypes.Structure):
 
 
 class vr_options(ctypes.Structure):
-    _fields_ = [("brick", ctypes.c_int32), ("pad_", ctypes.c_int32), ("step", ctypes.c_double),
+    _fields_ = [("brick", ctypes.c_int32), ("flags", ctypes.c_int32), ("step", ctypes.c_double),
                 ("ert", ctypes.c_double)]
 
 
@@ -157,11 +158,13 @@ def camera_struct(cam: dict) -> vr_camera:
 
 
 # ------------------------------------------------------------------ same-named entry points
-def vr_create(device: int = 0, brick: int = 128, step: float = 0.5, ert: float = 0.99):
+def vr_create(device: int = 0, brick: int = 128, step: float = 0.5, ert: float = 0.99,
+              single_store: bool = False):
     lib = load_library()
     o = vr_options()
     lib.vr_default_options(ctypes.byref(o))
     o.brick, o.step, o.ert = int(brick), float(step), float(ert)
+    o.flags = VR_OPT_SINGLE_STORE if single_store else 0
     h = ctypes.c_void_p()
     st = lib.vr_create(ctypes.byref(h), int(device), ctypes.byref(o))
     if st != VR_OK:
@@ -360,11 +363,12 @@ def vr_get_cube_info(ctx) -> dict:
 class Renderer:
     """A context plus its output buffers.  All rendering happens in libvr.so."""
 
-    def __init__(self, device: int = 0, brick: int = 128, step: float = 0.5, ert: float = 0.99):
+    def __init__(self, device: int = 0, brick: int = 128, step: float = 0.5, ert: float = 0.99,
+                 single_store: bool = False):
         import torch
         self.device = int(device)
         self.torch_device = torch.device("cuda", self.device)
-        self.ctx = vr_create(self.device, brick, step, ert)
+        self.ctx = vr_create(self.device, brick, step, ert, single_store)
         self.cams = []
 
     def close(self):

@@ -32,6 +32,7 @@ struct vr_ctx {
     long long slot_elems = 0;
     size_t elem = 4;
     void* pool = nullptr;
+    void* pool1 = nullptr;         // the store shifted by one element, when kept
     int* table = nullptr;
     unsigned int* minmax = nullptr;
     void* cells = nullptr;   // brick-pass cell list of the current view
@@ -162,10 +163,12 @@ void free_ooc(vr_ctx* c) {
 void free_cube(vr_ctx* c) {
     free_ooc(c);
     if (c->pool) cudaFree(c->pool);
+    if (c->pool1) cudaFree(c->pool1);
     if (c->table) cudaFree(c->table);
     if (c->minmax) cudaFree(c->minmax);
     if (c->cells) cudaFree(c->cells);
     c->pool = nullptr;
+    c->pool1 = nullptr;
     c->table = nullptr;
     c->minmax = nullptr;
     c->cells = nullptr;
@@ -175,6 +178,7 @@ void free_cube(vr_ctx* c) {
 VolDev vol_dev(const vr_ctx* c) {
     VolDev v{};
     v.pool = c->pool;
+    v.pool1 = c->pool1;
     v.table = c->table;
     v.nx = (int)c->nx;
     v.ny = (int)c->ny;
@@ -326,7 +330,7 @@ vr_status vr_create(vr_ctx** out, int device, const vr_options* opt) {
     vr_default_options(&o);
     if (opt) o = *opt;
     if (o.brick < 8 || o.brick > 256 || (o.brick & (o.brick - 1)) || !(o.step > 0.0) ||
-        !std::isfinite(o.step) || !(o.ert > 0.0) || !std::isfinite(o.ert))
+        !std::isfinite(o.step) || !(o.ert > 0.0) || !std::isfinite(o.ert) || (o.flags & ~VR_OPT_SINGLE_STORE))
         return VR_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -455,6 +459,23 @@ vr_status vr_load_cube(vr_ctx* ctx, const float* src, int src_on_device, int64_t
         VR_CK(cudaFreeAsync(stage, s), "vr_load_cube: staging free");
     }
     VR_CK(cudaStreamSynchronize(s), "vr_load_cube: repack");
+    if (!(ctx->opt.flags & VR_OPT_SINGLE_STORE)) {
+        // the copy shifted by one element, kept only when it fits in half of what is free
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && pool_bytes <= fr / 2) {
+            if (cudaMalloc(&ctx->pool1, pool_bytes) == cudaSuccess) {
+                const size_t e = (size_t)ctx->elem;
+                VR_CK(cudaMemcpyAsync(ctx->pool1, static_cast<char*>(ctx->pool) + e, pool_bytes - e,
+                                      cudaMemcpyDeviceToDevice, s), "vr_load_cube: shifted copy");
+                VR_CK(cudaMemsetAsync(static_cast<char*>(ctx->pool1) + pool_bytes - e, 0, e, s),
+                      "vr_load_cube: shifted copy");
+                VR_CK(cudaStreamSynchronize(s), "vr_load_cube: shifted copy");
+            } else {
+                cudaGetLastError();  // not kept: the single-store path serves every render
+                ctx->pool1 = nullptr;
+            }
+        }
+    }
     if (make_tensor_map(ctx)) {
         int cx, cy, cz;
         brick_cell_dims(ctx->dtype, &cx, &cy, &cz);
@@ -646,7 +667,7 @@ vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info) {
     info->pitch = ctx->pitch;
     info->dtype = ctx->dtype;
     info->brick_bytes = ctx->slot_elems * (long long)ctx->elem;
-    info->store_bytes = info->brick_bytes * (long long)ctx->nbx * ctx->nby * ctx->nbz;
+    info->store_bytes = info->brick_bytes * (long long)ctx->nbx * ctx->nby * ctx->nbz * (ctx->pool1 ? 2 : 1);
     return VR_OK;
 }
 
@@ -683,7 +704,7 @@ vr_status render_ray(vr_ctx* ctx, vr_mode mode, float* out_rgba, float* out_max,
     P.ert = (float)ctx->opt.ert;
     P.samples = ctx->sample_counter;
     const int block = ctx->tune.block;
-    const int grid = ctx->num_sms * march_blocks_per_sm(ctx->dtype, mode, block) * block / 32;
+    const int grid = ctx->num_sms * march_blocks_per_sm(ctx->dtype, mode, P.vol.pool1 != nullptr, block) * block / 32;
     const long long img = (long long)P.width * P.height;
     if (ctx->ev_start) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
     for (int b = 0; b < nbatch; ++b) {

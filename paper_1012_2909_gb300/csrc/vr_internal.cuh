@@ -30,6 +30,7 @@ struct CamDev {
 // element (z, y, x) of the slot at (z * rows + y) * pitch + x, x in [0, rows).
 struct VolDev {
     const void* pool;
+    const void* pool1; // the store shifted by one element (pool1[e] = pool[e + 1]), or null
     const int* table;  // linear brick id -> slot (-1 = not resident)
     int nx, ny, nz;
     int nbx, nby, nbz;
@@ -165,8 +166,9 @@ struct PixelParams {
 cudaError_t launch_repack(const float* src, long long src_z0, long long src_planes, int bz,
                           const VolDev& v, vr_dtype dt, void* pool, unsigned int* minmax,
                           cudaStream_t s);
+// The marcher reads x-neighbour pairs with one load when p.vol.pool1 is set.
 cudaError_t launch_march(const MarchParams& p, vr_dtype dt, int grid, int block, cudaStream_t s);
-int march_blocks_per_sm(vr_dtype dt, int mode, int block);
+int march_blocks_per_sm(vr_dtype dt, int mode, bool paired, int block);
 cudaError_t launch_pixel_setup(const PixelParams& p, cudaStream_t s);
 cudaError_t launch_mip_finalize(const PixelParams& p, cudaStream_t s);
 // `cells` is per-context scratch of brick_cells_bytes(units) bytes (a counter and the

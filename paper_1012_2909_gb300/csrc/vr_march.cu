@@ -1,10 +1,11 @@
 // Image-order ray marcher: one thread per ray, one warp per 8 x 4 pixel tile,
 // tiles handed out by a persistent scheduler (one atomic counter per launch).
 //
-// Per ray (the discretisation of include/vr.h, vr_render): double-precision
-// ray setup and box interval; brick-by-brick traversal, each segment anchored
-// in double precision and stepped in FP32 brick-local coordinates; trilinear
-// fetch from the ghosted brick; transfer-function lookup from shared memory;
+// Per ray (the discretisation of include/vr.h, vr_render): float-float ray
+// set-up and box interval; brick-by-brick traversal, each segment anchored in
+// float-float and stepped in FP32 brick-local coordinates; trilinear fetch from
+// the ghosted brick (x-neighbour pairs with one load each when the store's
+// shifted copy is kept); transfer-function lookup from shared memory;
 // front-to-back "over" with early termination, or maximum-intensity
 // projection.
 #include "vr_device.cuh"
@@ -20,7 +21,7 @@ constexpr int kSegCap = 128;  // samples between float-float re-anchors
 // capping registers at 64 for more warps cost 30 %.
 constexpr int kMarchUnroll = 4;
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool PAIRED>
 __global__ void __launch_bounds__(256, 1)
 k_march(const __grid_constant__ MarchParams P) {
     __shared__ float4 s_tf[kMaxTF];
@@ -31,6 +32,7 @@ k_march(const __grid_constant__ MarchParams P) {
     const int tiles_per_cam = P.tiles_x * P.tiles_y;
     const int total = tiles_per_cam * P.ncams;
     const T* __restrict__ pool = static_cast<const T*>(P.vol.pool);
+    const T* __restrict__ pool1 = static_cast<const T*>(P.vol.pool1);
     const float ert = P.ert;
     unsigned long long my_samples = 0;
 
@@ -57,6 +59,7 @@ k_march(const __grid_constant__ MarchParams P) {
                 Seg s;
                 seg_begin(r, k, P.vol, e32, kSegCap, s);
                 const T* slot = pool + s.base;
+                const T* slot1 = PAIRED ? pool1 + s.base : nullptr;
                 // kMarchUnroll samples fetched together (more loads in flight), then
                 // composited in order; a fetch past the segment repeats its last sample
                 for (int j = 0; j < s.n && !done; j += kMarchUnroll) {
@@ -64,8 +67,10 @@ k_march(const __grid_constant__ MarchParams P) {
 #pragma unroll
                     for (int q = 0; q < kMarchUnroll; ++q) {
                         const float fj = (float)min(j + q, s.n - 1);
-                        v[q] = fetch_trilinear<T>(slot, P.vol, fmaf(fj, e32.x, s.gx), fmaf(fj, e32.y, s.gy),
-                                                  fmaf(fj, e32.z, s.gz));
+                        const float gx = fmaf(fj, e32.x, s.gx), gy = fmaf(fj, e32.y, s.gy),
+                                    gz = fmaf(fj, e32.z, s.gz);
+                        v[q] = PAIRED ? fetch_trilinear_pair<T>(slot, slot1, P.vol, gx, gy, gz)
+                                      : fetch_trilinear<T>(slot, P.vol, gx, gy, gz);
                     }
 #pragma unroll
                     for (int q = 0; q < kMarchUnroll; ++q) {
@@ -109,28 +114,34 @@ k_march(const __grid_constant__ MarchParams P) {
 }
 
 template <typename T, int MODE>
-void* kernel_ptr() {
-    return reinterpret_cast<void*>(&k_march<T, MODE>);
+void* kernel_ptr(bool paired) {
+    return paired ? reinterpret_cast<void*>(&k_march<T, MODE, true>)
+                  : reinterpret_cast<void*>(&k_march<T, MODE, false>);
 }
 
-void* pick(vr_dtype dt, int mode) {
-    if (dt == VR_F32) return mode == VR_MIP ? kernel_ptr<float, VR_MIP>() : kernel_ptr<float, VR_COMPOSITE>();
-    if (dt == VR_F16) return mode == VR_MIP ? kernel_ptr<__half, VR_MIP>() : kernel_ptr<__half, VR_COMPOSITE>();
-    return mode == VR_MIP ? kernel_ptr<__nv_bfloat16, VR_MIP>() : kernel_ptr<__nv_bfloat16, VR_COMPOSITE>();
+template <typename T>
+void* pick_mode(int mode, bool paired) {
+    return mode == VR_MIP ? kernel_ptr<T, VR_MIP>(paired) : kernel_ptr<T, VR_COMPOSITE>(paired);
+}
+
+void* pick(vr_dtype dt, int mode, bool paired) {
+    if (dt == VR_F32) return pick_mode<float>(mode, paired);
+    if (dt == VR_F16) return pick_mode<__half>(mode, paired);
+    return pick_mode<__nv_bfloat16>(mode, paired);
 }
 
 }  // namespace
 
-int march_blocks_per_sm(vr_dtype dt, int mode, int block) {
+int march_blocks_per_sm(vr_dtype dt, int mode, bool paired, int block) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(dt, mode), block, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(dt, mode, paired), block, 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
 cudaError_t launch_march(const MarchParams& p, vr_dtype dt, int grid, int block, cudaStream_t s) {
     void* args[] = {const_cast<MarchParams*>(&p)};
-    return cudaLaunchKernel(pick(dt, p.mode), dim3(grid), dim3(block), args, 0, s);
+    return cudaLaunchKernel(pick(dt, p.mode, p.vol.pool1 != nullptr), dim3(grid), dim3(block), args, 0, s);
 }
 
 }  // namespace vr
