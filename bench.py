@@ -428,11 +428,19 @@ def extra_ooc(dev, cache_gib=32):
     warm = time.time() - t0
     st = vr.vr_get_stream_stats(r.ctx)
     r.close()
+    # the host-to-device link: one pinned 1 GiB buffer copied a few times
+    host = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
+    devb = torch.empty(1 << 28, dtype=torch.float32, device=f"cuda:{dev}")
+    h2d_ms = _events_ms(lambda: devb.copy_(host, non_blocking=True), 4)
+    h2d_gbs = host.numel() * 4 / (h2d_ms / 1e3) / 1e9
+    del host, devb
     return {"workload": "4096x4096x8192 FP16 (256 GiB) streamed from the generator, 32 GiB cache, "
                         "1920x1080, composite frame 0",
             "cold_frame_s": cold, "warm_frame_s": warm, "bricks_fetched": st0["bricks_fetched"],
             "bricks_culled": st0["bricks_culled"], "h2d_gb": st0["bytes_h2d"] / 1e9,
-            "generate_s": st0["generate_s"], "warm_refetched": st["bricks_fetched"] - st0["bricks_fetched"]}
+            "generate_s": st0["generate_s"], "warm_refetched": st["bricks_fetched"] - st0["bricks_fetched"],
+            "h2d_link_gbs": h2d_gbs, "h2d_floor_s": st0["bytes_h2d"] / 1e9 / h2d_gbs,
+            "generate_gbs": st0["bytes_h2d"] / 1e9 / max(st0["generate_s"], 1e-9)}
 
 
 # ------------------------------------------------------------------------------ our arm

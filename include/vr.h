@@ -124,9 +124,10 @@ typedef struct {
 } vr_options;
 
 /* vr_options.flags: keep one brick store only.  By default vr_load_cube also
- * keeps a copy of the store shifted by one element along x, when it fits in
- * half of the free device memory, so that the image-order marcher reads each
- * pair of x-neighbours of a trilinear fetch with one aligned load. */
+ * keeps, for FP16 and BF16 stores, a copy of the store shifted by one element
+ * along x when it fits in half of the free device memory, so that the
+ * image-order marcher's composite reads each pair of x-neighbours of a
+ * trilinear fetch with one aligned 32-bit load. */
 #define VR_OPT_SINGLE_STORE 1
 
 typedef struct vr_ctx vr_ctx;

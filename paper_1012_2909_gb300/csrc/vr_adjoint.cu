@@ -91,15 +91,15 @@ __device__ __forceinline__ void add_tf(float* __restrict__ g, int n, const TFGra
 }
 
 // One warp per ray, its lanes on 32 consecutive samples (a chunk).  A warp
-// claims a tile of 32 pixels, sets up their rays once (one lane each, FP64)
+// claims a tile of 32 pixels, sets up their rays once (one lane each, float-float)
 // into shared memory and then walks them.  Composite: the forward pass keeps
 // the transmittance at the start of every chunk (one float) and finds the
 // termination sample by a ballot on a warp prefix product of (1 - a); the
 // reverse pass recomputes each chunk from its checkpoint and gets the colour
 // and transmittance behind every sample from a warp suffix scan of "over",
 // carried from chunk to chunk.  MIP: a warp maximum per chunk keeps the first
-// maximal sample.  Sample positions: the FP64 ray split into float-float pairs
-// once, one float-float anchor per chunk, lane offsets in FP32, each lane
+// maximal sample.  Sample positions: the float-float ray from the set-up, one
+// float-float anchor per chunk, lane offsets in FP32, each lane
 // reading the brick that holds its sample (the ghost layer makes any brick
 // within half a voxel give the same value).
 struct RaySetup {
@@ -130,11 +130,11 @@ __device__ __forceinline__ int anchor_axis(ff p, const VolDev& v, int nb, float&
 
 __device__ __forceinline__ void lane_sample(const RaySetup& r, int k, int lane, float3 e32, const VolDev& v,
                                             LaneSample& s) {
-    const float fk = (float)k;  // exact: sample indices stay below 2^24
+    const ff fk = ff_of_int(k);  // exact for any sample index
     float gx, gy, gz;
-    const int bx0 = anchor_axis(ff_add(ff{r.o_hi[0], r.o_lo[0]}, ff_mul_f(ff{r.e_hi[0], r.e_lo[0]}, fk)), v, v.nbx, gx);
-    const int by0 = anchor_axis(ff_add(ff{r.o_hi[1], r.o_lo[1]}, ff_mul_f(ff{r.e_hi[1], r.e_lo[1]}, fk)), v, v.nby, gy);
-    const int bz0 = anchor_axis(ff_add(ff{r.o_hi[2], r.o_lo[2]}, ff_mul_f(ff{r.e_hi[2], r.e_lo[2]}, fk)), v, v.nbz, gz);
+    const int bx0 = anchor_axis(ff_add(ff{r.o_hi[0], r.o_lo[0]}, ff_mul(ff{r.e_hi[0], r.e_lo[0]}, fk)), v, v.nbx, gx);
+    const int by0 = anchor_axis(ff_add(ff{r.o_hi[1], r.o_lo[1]}, ff_mul(ff{r.e_hi[1], r.e_lo[1]}, fk)), v, v.nby, gy);
+    const int bz0 = anchor_axis(ff_add(ff{r.o_hi[2], r.o_lo[2]}, ff_mul(ff{r.e_hi[2], r.e_lo[2]}, fk)), v, v.nbz, gz);
     const float fl = (float)lane;
     gx = fmaf(fl, e32.x, gx);
     gy = fmaf(fl, e32.y, gy);

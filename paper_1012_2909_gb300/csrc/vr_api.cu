@@ -459,8 +459,10 @@ vr_status vr_load_cube(vr_ctx* ctx, const float* src, int src_on_device, int64_t
         VR_CK(cudaFreeAsync(stage, s), "vr_load_cube: staging free");
     }
     VR_CK(cudaStreamSynchronize(s), "vr_load_cube: repack");
-    if (!(ctx->opt.flags & VR_OPT_SINGLE_STORE)) {
-        // the copy shifted by one element, kept only when it fits in half of what is free
+    if (storage != VR_F32 && !(ctx->opt.flags & VR_OPT_SINGLE_STORE)) {
+        // the copy shifted by one element (16-bit stores: an x-pair is one 32-bit load;
+        // FP32 pairs as 64-bit loads measured no faster), kept only when it fits in half
+        // of what is free
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && pool_bytes <= fr / 2) {
             if (cudaMalloc(&ctx->pool1, pool_bytes) == cudaSuccess) {

@@ -300,11 +300,11 @@ __device__ __forceinline__ bool make_segment(const BrickParams& P, const CamFF& 
             E[a] = ff_mul(ff{c.dir_hi[a], c.dir_lo[a]}, ff{P.step, P.step_lo});
         }
     }
-    const float fk = (float)ka;
+    const ff fk = ff_of_int(ka);
     float g[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const ff p = ff_add(O[a], ff_mul_f(E[a], fk));
+        const ff p = ff_add(O[a], ff_mul(E[a], fk));
         g[a] = __fadd_rn(__fsub_rn(p.hi, lo3[a]), p.lo) + 0.5f;
     }
     // Samples lie on the segment between the first and the last one, so if both

@@ -237,9 +237,6 @@ __device__ __forceinline__ float fetch_trilinear(const T* __restrict__ slot, con
 
 // Word w of a slot read as a pair of adjacent voxels (x, x + 1), widened to FP32.
 template <typename T> __device__ __forceinline__ float2 ld_pair(const T* p, int w);
-template <> __device__ __forceinline__ float2 ld_pair<float>(const float* p, int w) {
-    return __ldg(reinterpret_cast<const float2*>(p) + w);
-}
 template <> __device__ __forceinline__ float2 ld_pair<__half>(const __half* p, int w) {
     return __half22float2(__ldg(reinterpret_cast<const __half2*>(p) + w));
 }

@@ -20,7 +20,8 @@
 // eye's brick index e on every axis, so the key sum_a |b_a - e_a|
 // (perspective) or sum_a sign(d_a) b_a (orthographic) strictly increases along
 // every ray.  Sample ownership per brick uses the same FP32 face-crossing
-// partition as the cell pass, clipped to the ray's FP64 sample range.
+// partition as the cell pass, clipped to the ray's sample range from the
+// pixel set-up.
 #include <algorithm>
 
 #include "vr_device.cuh"
@@ -214,10 +215,10 @@ __device__ __forceinline__ bool brick_segment(const SortParams& P, int px, int p
             E[a] = ff_mul(ff{c.dir_hi[a], c.dir_lo[a]}, ff{P.step, P.step_lo});
         }
     }
-    const float fk = (float)ka;
+    const ff fk = ff_of_int(ka);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const ff p = ff_add(O[a], ff_mul_f(E[a], fk));
+        const ff p = ff_add(O[a], ff_mul(E[a], fk));
         g[a] = __fadd_rn(__fsub_rn(p.hi, (float)(bi[a] * B)), p.lo) + 0.5f;  // slot coordinate
         e32[a] = E[a].hi;
     }
