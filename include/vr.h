@@ -231,7 +231,7 @@ vr_status vr_render_backward(vr_ctx* ctx, vr_mode mode, const float* dL_dimg, fl
  *   block:           threads per CTA of the image-order path (64, 128, 256);
  *   group:           lanes per ray segment in the brick path (4, 8, 16), i.e.
  *                    32 / group rays per warp.
- * Defaults 8 x 4, 128, 8.  Results do not depend on the tuning. */
+ * Defaults 8 x 4, 256, 8.  Results do not depend on the tuning. */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t block;

@@ -65,7 +65,7 @@ struct vr_ctx {
     CUtensorMap tmap;
     bool has_tmap = false;
     vr_path path = VR_PATH_AUTO;
-    vr_tuning tune{8, 4, 128, 8};  // tile_w, tile_h, block, group
+    vr_tuning tune{8, 4, 256, 8};  // tile_w, tile_h, block, group
     bool graph_mode = false;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;

@@ -181,7 +181,6 @@ size_t brick_cells_bytes(long long nunits);
 void brick_cell_dims(vr_dtype dt, int* cx, int* cy, int* cz);
 // TMA box of one cell (cell + 2 ghost, x padded to 16 bytes), in elements.
 void brick_box_dims(vr_dtype dt, int* bx, int* by, int* bz);
-constexpr int kMarchThreads = 128;
 cudaError_t launch_brick_footprints(const SortParams& p, cudaStream_t s);
 cudaError_t launch_brick_partial(const SortParams& p, vr_dtype dt, bool carried, int l0, int l1, int grid,
                                  cudaStream_t s);
