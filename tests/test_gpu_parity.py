@@ -110,6 +110,40 @@ def test_odd_step_sizes(vr, step):
             assert st["nsamples"] > 0
 
 
+@pytest.mark.parametrize("ntf,ert,vrange", [(2, 0.05, (-1.0, 20.0)), (1024, 2.0, (-1.0, 20.0)),
+                                             (1024, 0.5, (2.0, 3.0))])
+def test_transfer_function_and_termination_extremes(vr, ntf, ert, vrange):
+    """The smallest (2 entries) and largest (1024) tables, termination after the first
+    few samples (ert 0.05), termination disabled (ert > 1), and a narrow value range that
+    clamps most samples at both ends: every path against the oracle."""
+    dims = (45, 37, 71)
+    vol = synth.generate(synth.cube_params(*dims, seed=9, nsrc=8))
+    tf = synth.hidden_tf(17, ntf)
+    cams = [synth.orbit_view(dims, 41.0, 41, 29), synth.ortho_view(dims, 41, 29)]
+    sc = oracle.Scene(vol, tf, vrange[0], vrange[1], 0.5, ert)
+    for mode, path in (("composite", "ray"), ("mip", "ray"), ("mip", "brick")):
+        img, mx = _render(vr, vol, tf, cams, mode, brick=32, ert=ert, vmin=vrange[0], vmax=vrange[1],
+                          path=path)
+        for i, c in enumerate(cams):
+            compare(img[i].reshape(-1, 4), sc, c, mode, tol=1e-4,
+                    gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
+
+
+def test_fine_step(vr):
+    """A step of 0.05 voxel (20 samples per voxel, thousands per ray), every path."""
+    dims = (24, 20, 36)
+    vol = synth.generate(synth.cube_params(*dims, seed=10, nsrc=4))
+    tf = synth.viridis_ramp_tf()
+    cams = [synth.orbit_view(dims, 77.0, 24, 18), synth.ortho_view(dims, 24, 18)]
+    sc = oracle.Scene(vol, tf, -1.0, 20.0, 0.05, 0.99)
+    for mode, path in (("composite", "ray"), ("mip", "ray"), ("mip", "brick")):
+        img, mx = _render(vr, vol, tf, cams, mode, brick=8 if path == "ray" else 32, step=0.05, path=path)
+        for i, c in enumerate(cams):
+            st = compare(img[i].reshape(-1, 4), sc, c, mode, tol=1e-4,
+                         gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
+            assert st["nsamples"] > 0
+
+
 def test_distant_narrow_view(vr):
     """An eye ~1e5 voxels away with a 0.02 degree field of view: the FP32 screen of the
     sample range fails for most rays, so the float-float slab test decides them, and the
