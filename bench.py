@@ -500,13 +500,14 @@ def run_ours(a):
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(a.steps)]
 
-    def step(r, i, kernel_events=None):
+    def step(r, i, kernel_events=None, bufs=None):
         f = i % len(cams)
+        oc, om, mm = bufs if bufs is not None else (out_c, out_m, max_m)
         r.set_camera(cams[f])
-        r.render("composite", out=out_c)
+        r.render("composite", out=oc)
         if kernel_events is not None:
             vr.vr_set_kernel_events(r.ctx, *kernel_events)
-        r.render("mip", out=out_m, out_max=max_m, with_max=True)
+        r.render("mip", out=om, out_max=mm, with_max=True)
         if kernel_events is not None:
             vr.vr_set_kernel_events(r.ctx, None, None)
         return nsamp["composite"][f] + nsamp["mip"][f]
@@ -542,20 +543,40 @@ def run_ours(a):
     (ms, ms32), total_samples = aggregate([ms, ms32], samples, world, f"cuda:{dev}")
 
     # end to end through the public API: camera from the host in, both images out to
-    # pinned host memory, every step
-    host_c = torch.empty((1, H, W, 4), pin_memory=True)
-    host_m = torch.empty((1, H, W, 4), pin_memory=True)
+    # pinned host memory, every step.  Double-buffered as an application would run it:
+    # step i renders into buffer set i % 2 while a copy stream reads step i - 1 back.
+    bufs = [(torch.empty_like(out_c), torch.empty_like(out_m), torch.empty_like(max_m)) for _ in range(2)]
+    hosts = [(torch.empty((1, H, W, 4), pin_memory=True), torch.empty((1, H, W, 4), pin_memory=True))
+             for _ in range(2)]
+    cstream = torch.cuda.Stream()
+    rendered = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    main = torch.cuda.current_stream()
+
+    def e2e_step(i):
+        b = i % 2
+        if i >= 2:
+            main.wait_event(copied[b])  # the read-back of step i - 2 has left buffer set b
+        n = step(rq, i, bufs=bufs[b])
+        rendered[b].record(main)
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(rendered[b])
+            hosts[b][0].copy_(bufs[b][0], non_blocking=True)
+            hosts[b][1].copy_(bufs[b][1], non_blocking=True)
+            copied[b].record(cstream)
+        return n
+
     for i in range(a.warmup):
-        step(rq, i)
+        e2e_step(i)
     torch.cuda.synchronize()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     esamples = 0
     for i in range(a.steps):
-        esamples += step(rq, i)
-        host_c.copy_(out_c, non_blocking=True)
-        host_m.copy_(out_m, non_blocking=True)
+        esamples += e2e_step(i)
+    for b in range(2):
+        main.wait_event(copied[b])  # every read-back is inside the timed region
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
