@@ -73,3 +73,31 @@ def test_pyramid_layout_matches_the_oracle():
     for bad in ((0, 5, 0), (5, 0, 0), (4, 4, 12), (4, 4, 4), (4, 4, 8192)):
         with pytest.raises(vr.VrError):
             vr.vr_pyramid_layout(*bad)
+
+
+def _code(path):
+    """Source text without comments."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    return re.sub(r"//[^\n]*", " ", text)
+
+
+def test_device_code_keeps_fp64_to_the_table_gradient_reduction():
+    """The render and adjoint kernels compute in FP32 and float-float pairs: `double`
+    appears in no device source except the body of the final table-gradient reduction
+    (k_tfgrad_reduce) and the catalogue overlay, which is off the render path and follows
+    the oracle's double-precision projection.  vr_api.cu and the host structs of
+    vr_internal.cuh are host code."""
+    csrc = os.path.join(ROOT, "paper_1012_2909_gb300", "csrc")
+    host_or_exempt = {"vr_api.cu", "vr_overlay.cu", "vr_internal.cuh"}
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        name = os.path.basename(path)
+        if name in host_or_exempt:
+            continue
+        code = _code(path)
+        if name == "vr_adjoint.cu":
+            start = code.index("k_tfgrad_reduce(")
+            body_end = code.index("\n}", start)
+            assert re.search(r"\bdouble\b", code[start:body_end])
+            code = code[:start] + code[body_end:]
+        assert not re.search(r"\bdouble\b", code), name
