@@ -182,7 +182,9 @@ vr_status vr_load_cube(vr_ctx* ctx, const float* src, int src_on_device, int64_t
 vr_status vr_set_transfer_function(vr_ctx* ctx, const float* rgba, int n, float vmin,
                                    float vmax);
 
-/* Set ncams (1..4096) cameras from HOST memory, all of one width x height. */
+/* Set ncams (1..4096) cameras from HOST memory, all of one width x height
+ * (width, height <= 65536, width * height <= 2^30, ncams * width * height
+ * <= 2^40; VR_ERR_INVALID_ARG otherwise). */
 vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams);
 
 /*

@@ -2,6 +2,7 @@
 // transfer function, cameras and render dispatch.  No exception crosses the
 // boundary; every failure becomes a vr_status with a message on the context.
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <thread>
 #include <cmath>
@@ -635,7 +636,8 @@ vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams) {
         d.height = c.height;
         d.pad = 0;
     }
-    if ((long long)ncams * cams[0].width * cams[0].height > (1LL << 40))
+    if ((long long)cams[0].width * cams[0].height > (1LL << 30) ||
+        (long long)ncams * cams[0].width * cams[0].height > (1LL << 40))
         return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: too many pixels");
     ctx->cams.swap(out);
     return VR_OK;
@@ -747,7 +749,9 @@ vr_status render_brick_mip(vr_ctx* ctx, float* out_rgba, float* out_max, cudaStr
     const int W = ctx->cams[0].width, H = ctx->cams[0].height;
     const long long img = (long long)W * H;
     const int ncams = (int)ctx->cams.size();
-    const int per = std::min(ncams, kMaxLaunchCams);
+    // cameras per pass: at most kMaxLaunchCams, and few enough that a pixel index of the
+    // pass (camera * W * H + pixel) fits an int
+    const int per = (int)std::min<long long>(std::min(ncams, kMaxLaunchCams), std::max(1LL, INT_MAX / img));
     vr_status st = ensure_pixel_scratch(ctx, img * per);
     if (st != VR_OK) return st;
     PixelParams pp;
