@@ -270,6 +270,16 @@ vr_status vr_set_path(vr_ctx* ctx, vr_path path);
  * samples it executed (VR_PATH_RAY only); NULL switches counting off. */
 vr_status vr_set_sample_counter(vr_ctx* ctx, unsigned long long* device_counter);
 
+/* Failure-detection self-test.  Runs, on `stream`, one thread that waits with
+ * the brick pass's bounded mbarrier wait (shortened to 2^14 polls) on a barrier
+ * phase that no copy will complete, so that the wait gives up and records the
+ * device status word exactly as an expired wait of a render would; then
+ * synchronises the stream.  Returns VR_OK once the status word is set (the
+ * next vr_render or vr_render_mip_noalloc reports VR_ERR_INTERNAL once and
+ * clears it; the context stays usable), VR_ERR_INTERNAL if the wait did not
+ * expire, VR_ERR_CUDA on a launch error. */
+vr_status vr_selftest_wait_timeout(vr_ctx* ctx, void* stream);
+
 /* Profiling hook: when both are non-NULL, vr_render records the CUDA events
  * `start` and `stop` (cudaEvent_t, created by the caller) on its stream just
  * before the first and just after the last launch of its dominant kernel (the

@@ -100,6 +100,7 @@ SIGNATURES = {
     "vr_set_graph": (ctypes.c_int, [_P, ctypes.c_int]),
     "vr_render_backward": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P]),
     "vr_set_sample_counter": (ctypes.c_int, [_P, _P]),
+    "vr_selftest_wait_timeout": (ctypes.c_int, [_P, _P]),
     "vr_set_kernel_events": (ctypes.c_int, [_P, _P, _P]),
     "vr_render_mip_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "vr_get_cube_info": (ctypes.c_int, [_P, _P]),
@@ -332,6 +333,13 @@ def vr_set_stream_timeout(ctx, seconds: float):
 def vr_set_path(ctx, path: str = "auto"):
     st = load_library().vr_set_path(ctx, PATHS[path])
     _check(ctx, st, "vr_set_path")
+
+
+def vr_selftest_wait_timeout(ctx, stream=None, device: int = 0):
+    """Make one bounded device wait expire on purpose (no copy in flight) and leave its
+    status for the next render to report."""
+    st = load_library().vr_selftest_wait_timeout(ctx, _stream_handle(stream, device))
+    _check(ctx, st, "vr_selftest_wait_timeout")
 
 
 def vr_set_sample_counter(ctx, counter=None):

@@ -17,6 +17,7 @@
 #include <cudaTypedefs.h>
 
 #include "vr_internal.cuh"
+#include "vr_tma.cuh"
 
 using namespace vr;
 
@@ -640,6 +641,18 @@ vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams) {
         (long long)ncams * cams[0].width * cams[0].height > (1LL << 40))
         return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: too many pixels");
     ctx->cams.swap(out);
+    return VR_OK;
+}
+
+vr_status vr_selftest_wait_timeout(vr_ctx* ctx, void* stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    VR_CK(cudaGetLastError(), "vr_selftest_wait_timeout: pending CUDA error");
+    VR_CK(launch_wait_probe(ctx->status_dev, 1LL << 14, s), "vr_selftest_wait_timeout: launch");
+    VR_CK(cudaStreamSynchronize(s), "vr_selftest_wait_timeout: wait");
+    if (*ctx->status_host != (int)kDevWaitTimeout)
+        return fail(ctx, VR_ERR_INTERNAL, "vr_selftest_wait_timeout: the bounded wait did not expire");
     return VR_OK;
 }
 

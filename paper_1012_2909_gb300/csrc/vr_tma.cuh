@@ -50,9 +50,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false (and *status set) on expiry.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
-    for (long long i = 0; i < kWaitSpinLimit; ++i)
+// Bounded wait for phase `parity` of `bar`; false (and *status set) after
+// `limit` unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status,
+                                          long long limit = kWaitSpinLimit) {
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     if (status) atomicExch(status, (int)kDevWaitTimeout);
     return false;
