@@ -179,7 +179,8 @@ size_t brick_cells_bytes(long long nunits);
 // Cell (staging unit) edge lengths for a storage type; the brick edge must be a
 // multiple of each.
 void brick_cell_dims(vr_dtype dt, int* cx, int* cy, int* cz);
-// TMA box of one cell (cell + 2 ghost, x padded to 16 bytes), in elements.
+// TMA box of one cell (cell + 2 ghost, x padded to 16 bytes, one spare row for
+// 16-bit stores), in elements.
 void brick_box_dims(vr_dtype dt, int* bx, int* by, int* bz);
 cudaError_t launch_brick_footprints(const SortParams& p, cudaStream_t s);
 cudaError_t launch_brick_partial(const SortParams& p, vr_dtype dt, bool carried, int l0, int l1, int grid,
