@@ -17,13 +17,17 @@ namespace {
 constexpr int kSegCap = 128;  // samples between float-float re-anchors
 // Samples fetched together per step.  The marcher waits on its gathers, so more
 // loads in flight beat more resident warps: with the register count left free
-// (launch bound 256 x 1), 4 measured fastest (3: +2 %, 6: +2 %, 2: +9 %), and
-// capping registers at 64 for more warps cost 30 %.
+// (launch bound 256 x 1), 4 measured fastest for single loads (3: +2 %, 6: +2 %,
+// 2: +9 %; capping registers at 64 for more warps cost 30 %), and 6 with the
+// paired loads, which need fewer registers per sample (4: +7 %, 3: +13 %,
+// 8: +15 %; survey composite over the orbit).
 constexpr int kMarchUnroll = 4;
+constexpr int kMarchUnrollPaired = 6;
 
 template <typename T, int MODE, bool PAIRED>
 __global__ void __launch_bounds__(256, 1)
 k_march(const __grid_constant__ MarchParams P) {
+    constexpr int U = PAIRED ? kMarchUnrollPaired : kMarchUnroll;
     __shared__ float4 s_tf[kMaxTF];
     for (int i = threadIdx.x; i < P.tf.n; i += blockDim.x) s_tf[i] = P.tf.tab[i];
     __syncthreads();
@@ -60,12 +64,12 @@ k_march(const __grid_constant__ MarchParams P) {
                 seg_begin(r, k, P.vol, e32, kSegCap, s);
                 const T* slot = pool + s.base;
                 const T* slot1 = PAIRED ? pool1 + s.base : nullptr;
-                // kMarchUnroll samples fetched together (more loads in flight), then
+                // U samples fetched together (more loads in flight), then
                 // composited in order; a fetch past the segment repeats its last sample
-                for (int j = 0; j < s.n && !done; j += kMarchUnroll) {
-                    float v[kMarchUnroll];
+                for (int j = 0; j < s.n && !done; j += U) {
+                    float v[U];
 #pragma unroll
-                    for (int q = 0; q < kMarchUnroll; ++q) {
+                    for (int q = 0; q < U; ++q) {
                         const float fj = (float)min(j + q, s.n - 1);
                         const float gx = fmaf(fj, e32.x, s.gx), gy = fmaf(fj, e32.y, s.gy),
                                     gz = fmaf(fj, e32.z, s.gz);
@@ -73,7 +77,7 @@ k_march(const __grid_constant__ MarchParams P) {
                                       : fetch_trilinear<T>(slot, P.vol, gx, gy, gz);
                     }
 #pragma unroll
-                    for (int q = 0; q < kMarchUnroll; ++q) {
+                    for (int q = 0; q < U; ++q) {
                         if (j + q >= s.n) break;
                         if (MODE == VR_MIP) {
                             m = fmaxf(m, v[q]);
