@@ -34,7 +34,7 @@ def _setup(dims, nviews, size, seed, storage="f32", ntf=64, step=0.5):
 
 
 @pytest.mark.parametrize("mode", ["composite", "mip"])
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("step", [0.5, 0.37])
 def test_gradients_match_oracle(mode, storage, step):
     dims = (24, 20, 28)

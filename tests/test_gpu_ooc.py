@@ -36,7 +36,7 @@ def _streamed(vr, p, storage, cache_bricks, brick=32):
     return r
 
 
-@pytest.mark.parametrize("storage", ["f16", "f32"])
+@pytest.mark.parametrize("storage", ["f16", "bf16", "f32"])
 def test_streamed_equals_oracle_and_in_core(cube, storage):
     import paper_1012_2909_gb300 as vr
     p, vol = cube

@@ -374,7 +374,7 @@ def test_survey_workload_sampled_pixels(vr, storage):
     r.close()
 
 
-@pytest.mark.parametrize("storage", ["f16"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_wall_25_frusta_one_launch(vr, storage):
     """5 x 5 wall: 25 off-axis frusta of one camera rendered together (one persistent
     launch per mode); each panel equals the oracle, and the mosaic equals the oracle's
@@ -397,7 +397,7 @@ def test_wall_25_frusta_one_launch(vr, storage):
                     gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_sortlast_and_layered_composite(vr, storage):
     """Object-order composite: per-brick partial images folded in visibility order equal
     the oracle's composite without termination; the layered form (running state carried
