@@ -118,3 +118,33 @@ def test_cache_smaller_than_a_brick_is_rejected(cube):
         vr.vr_load_cube_streamed(r.ctx, fn, user, DIMS, "f16", cache_bytes=1000)
     assert e.value.status == vr.VR_ERR_INVALID_ARG
     r.close()
+
+
+def test_cache_beyond_device_memory_is_out_of_memory(cube):
+    """A brick cache that cannot be allocated (a 32768^3 cube with a 1 PB budget) answers
+    VR_ERR_OOM without calling the region callback, and the same context then loads and
+    renders a cube correctly."""
+    import paper_1012_2909_gb300 as vr
+    p, vol = cube
+    r = vr.Renderer(0, brick=32)
+    calls = []
+
+    @vr.REGION_FN
+    def never(user, x0, y0, z0, sx, sy, sz, out):
+        calls.append(1)
+        return 1
+
+    with pytest.raises(vr.VrError) as e:
+        vr.vr_load_cube_streamed(r.ctx, never, None, (1 << 15, 1 << 15, 1 << 15), "f16", cache_bytes=1 << 50)
+    assert e.value.status == vr.VR_ERR_OOM
+    assert not calls
+    tf = synth.viridis_ramp_tf()
+    cam = synth.orbit_view(DIMS, 75.0, 48, 36)
+    r.load_cube(vol, "f16")
+    r.set_transfer_function(tf, -1.0, 20.0)
+    r.set_camera(cam)
+    img = r.render("composite")
+    torch.cuda.synchronize()
+    sc = oracle.Scene(oracle.round_storage(vol, "f16"), tf, -1.0, 20.0, 0.5, 0.99)
+    compare(img[0].cpu().numpy().reshape(-1, 4), sc, cam, "composite", tol=1e-4)
+    r.close()
