@@ -43,9 +43,12 @@ __device__ __forceinline__ ff slab_t(ff x, ff d) {
     return ff_div(x, d);
 }
 
+// Ray of pixel (px, py) and its sample range [k0, k1); false when the ray has no
+// sample in the box (then k0 = k1 = 0).
 __device__ __forceinline__ bool make_ray(const CamFF& c, int px, int py, const VolDev& v, ff step, Ray& r) {
     const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
     const bool persp = c.type == 1;
+    const ff nx[3] = {ff_of_int(v.nx), ff_of_int(v.ny), ff_of_int(v.nz)};  // exact box extents
     ff V[3];  // perspective: direction (unnormalised); orthographic: origin
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -114,7 +117,7 @@ __device__ __forceinline__ bool make_ray(const CamFF& c, int px, int py, const V
         for (int a = 0; a < 3; ++a) {
             const float o = r.o[a].hi, d = dn[a].hi;
             if (d == 0.f) {  // exactly parallel (hi == 0 means the pair is 0)
-                if (o < 0.f || ff_lt(ff{nf[a], 0.f}, r.o[a])) return false;
+                if (o < 0.f || ff_lt(nx[a], r.o[a])) return false;
                 continue;
             }
             const float t1 = (0.f - o) / d, t2 = (nf[a] - o) / d;
@@ -153,7 +156,7 @@ __device__ __forceinline__ bool make_ray(const CamFF& c, int px, int py, const V
     for (int a = 0; a < 3; ++a) {
         if (dn[a].hi == 0.f) continue;  // inside its slab (checked above)
         const ff t1 = slab_t(ff_neg(r.o[a]), dn[a]);
-        const ff t2 = slab_t(ff_add(ff{nf[a], 0.f}, ff_neg(r.o[a])), dn[a]);
+        const ff t2 = slab_t(ff_add(nx[a], ff_neg(r.o[a])), dn[a]);
         const bool sw = ff_lt(t2, t1);
         const ff tl = sw ? t2 : t1, th = sw ? t1 : t2;
         if (ff_lt(lo, tl)) lo = tl;
