@@ -102,7 +102,8 @@ typedef enum {
  * output size" is the same camera with another width/height).
  * All cameras passed together must have the same width and height.
  * Every component of eye, right, up, fwd and win must be finite and at most
- * 1e9 in magnitude (VR_ERR_INVALID_ARG otherwise).  Rays are set up in
+ * 1e9 in magnitude, and right, up, fwd must span space (VR_ERR_INVALID_ARG
+ * otherwise).  Rays are set up in
  * float-float arithmetic (about 44 bits): a sample up to 1e6 voxels from the
  * ray origin lies within ~1e-7 voxel of its exact position.
  */

@@ -270,7 +270,9 @@ bool cam_ff(const CamDev& d, CamFF& f) {
     const double m[9] = {R[0], U[0], F[0], R[1], U[1], F[1], R[2], U[2], F[2]};
     const double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
                        m[2] * (m[3] * m[7] - m[4] * m[6]);
-    if (!(std::fabs(det) > 1e-12)) return false;
+    const double scale = std::sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]) *
+                         std::sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]) * fl;
+    if (!(std::fabs(det) > 1e-12 * scale)) return false;
     const double inv[9] = {(m[4] * m[8] - m[5] * m[7]) / det, (m[2] * m[7] - m[1] * m[8]) / det,
                            (m[1] * m[5] - m[2] * m[4]) / det, (m[5] * m[6] - m[3] * m[8]) / det,
                            (m[0] * m[8] - m[2] * m[6]) / det, (m[2] * m[3] - m[0] * m[5]) / det,
@@ -617,8 +619,20 @@ vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams) {
         if (beyond(c.eye, 3, 1e9) || beyond(c.right, 3, 1e9) || beyond(c.up, 3, 1e9) || beyond(c.fwd, 3, 1e9) ||
             beyond(c.win, 4, 1e9))
             return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: a camera value is beyond 1e9 in magnitude");
-        if (c.type == 0 && c.fwd[0] == 0.0 && c.fwd[1] == 0.0 && c.fwd[2] == 0.0)
-            return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: zero forward vector");
+        {
+            // right, up and fwd must span space: otherwise every ray of a perspective view lies
+            // in one plane and a pixel direction can vanish (orthographic: no direction at all)
+            const double* R = c.right;
+            const double* U = c.up;
+            const double* F = c.fwd;
+            const double det = R[0] * (U[1] * F[2] - U[2] * F[1]) - U[0] * (R[1] * F[2] - R[2] * F[1]) +
+                               F[0] * (R[1] * U[2] - R[2] * U[1]);
+            const double scale = std::sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]) *
+                                 std::sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]) *
+                                 std::sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+            if (!(std::fabs(det) > 1e-12 * scale))
+                return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: right, up and fwd do not span space");
+        }
         if (c.win[1] == c.win[0] || c.win[3] == c.win[2])
             return fail(ctx, VR_ERR_INVALID_ARG, "vr_set_camera: empty window");
         CamDev& d = out[(size_t)i];

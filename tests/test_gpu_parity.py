@@ -300,6 +300,10 @@ def test_status_codes(vr):
     with pytest.raises(vr.VrError) as e:  # beyond the float-float set-up's range
         r.set_camera(far)
     assert e.value.status == vr.VR_ERR_INVALID_ARG
+    flat = dict(synth.orbit_view((8, 8, 8), 0.0, 4, 4), fwd=[0.0, 0.0, 0.0])  # no forward axis
+    with pytest.raises(vr.VrError) as e:
+        r.set_camera(flat)
+    assert e.value.status == vr.VR_ERR_INVALID_ARG
     huge = synth.orbit_view((8, 8, 8), 0.0, 32768, 32769)  # more than 2^30 pixels in one image
     with pytest.raises(vr.VrError) as e:
         r.set_camera(huge)
