@@ -396,7 +396,8 @@ vr_status vr_image_pyramid(vr_ctx* ctx, const float* rgba, int32_t width, int32_
  * hide groups of boxes by what is passed.  Stream-ordered on `stream`; the
  * host arrays may be reused when the call returns.
  * Errors: VR_ERR_INVALID_ARG for NULL or misaligned arrays, cameras of
- * different sizes, a bad camera type or an empty window.
+ * different sizes, a bad camera type, an empty window, a non-finite camera
+ * or box value, or more than 2^30 pixels per image.
  */
 vr_status vr_overlay_boxes(vr_ctx* ctx, const vr_camera* cams, int32_t ncams, const double* boxes, int64_t nbox,
                            const float* colours, float* rgba, void* stream);

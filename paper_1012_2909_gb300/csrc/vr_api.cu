@@ -1674,6 +1674,9 @@ vr_status vr_overlay_boxes(vr_ctx* ctx, const vr_camera* cams, int32_t ncams, co
             !(c.win[1] != c.win[0]) || !(c.win[3] != c.win[2]))
             return fail(ctx, VR_ERR_INVALID_ARG, "vr_overlay_boxes: cameras need one positive size, a type "
                                                  "and a window of positive extent");
+        if (!finite3(c.eye) || !finite3(c.right) || !finite3(c.up) || !finite3(c.fwd) || !finite3(c.win) ||
+            !std::isfinite(c.win[3]) || (long long)W * H > (1LL << 30))
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_overlay_boxes: non-finite camera or more than 2^30 pixels");
         OverlayCam& o = oc[(size_t)i];
         std::memset(&o, 0, sizeof(o));
         for (int a = 0; a < 3; ++a) {
@@ -1690,6 +1693,8 @@ vr_status vr_overlay_boxes(vr_ctx* ctx, const vr_camera* cams, int32_t ncams, co
         o.width = W;
         o.height = H;
     }
+    for (long long i = 0; i < 6 * nbox; ++i)
+        if (!std::isfinite(boxes[i])) return fail(ctx, VR_ERR_INVALID_ARG, "vr_overlay_boxes: non-finite box");
     DevGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long npix = (long long)ncams * W * H;

@@ -107,4 +107,13 @@ def test_bad_arguments(vr):
     with pytest.raises(vr.VrError) as e:
         r.overlay(torch.zeros((2, 8, 8, 4), device="cuda"), box, col, cams=[c, c2])
     assert e.value.status == vr.VR_ERR_INVALID_ARG
+    img = torch.zeros((1, 8, 8, 4), device="cuda")
+    with pytest.raises(vr.VrError) as e:  # a non-finite box is refused, the image is untouched
+        r.overlay(img, np.array([[1, 1, 1, np.nan, 5, 5.0]]), col, cams=[c])
+    assert e.value.status == vr.VR_ERR_INVALID_ARG
+    with pytest.raises(vr.VrError) as e:
+        r.overlay(img, box, col, cams=[dict(c, eye=[0.0, np.inf, -10.0])])
+    assert e.value.status == vr.VR_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert not img.any()
     r.close()
