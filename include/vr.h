@@ -370,8 +370,8 @@ vr_status vr_set_stream_timeout(vr_ctx* ctx, double seconds);
  * zeros where an edge tile passes the level.  Stream-ordered on `stream`.
  * vr_pyramid_layout returns L (levels counting level 0) and the number of
  * floats out must hold (0 for a 1 x 1 image); either pointer may be NULL.
- * Errors: VR_ERR_INVALID_ARG for non-positive sizes, a bad tile, NULL or
- * misaligned images.  The paper's file formats are not written here.
+ * Errors: VR_ERR_INVALID_ARG for sizes outside [1, 2^20], a bad tile, NULL
+ * or misaligned images.  The paper's file formats are not written here.
  */
 vr_status vr_pyramid_layout(int32_t width, int32_t height, int32_t tile, int32_t* levels, int64_t* floats);
 vr_status vr_image_pyramid(vr_ctx* ctx, const float* rgba, int32_t width, int32_t height, int32_t tile,

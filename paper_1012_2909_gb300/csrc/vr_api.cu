@@ -1632,7 +1632,7 @@ int tile_log2(int32_t tile) {
 
 vr_status vr_pyramid_layout(int32_t width, int32_t height, int32_t tile, int32_t* levels, int64_t* floats) {
     const int tl = tile_log2(tile);
-    if (width <= 0 || height <= 0 || tl == -2) return VR_ERR_INVALID_ARG;
+    if (width <= 0 || height <= 0 || width > (1 << 20) || height > (1 << 20) || tl == -2) return VR_ERR_INVALID_ARG;
     std::vector<int> ws, hs;
     std::vector<long long> offs;
     const long long n = pyramid_levels(width, height, tl, ws, hs, offs);
@@ -1645,8 +1645,8 @@ vr_status vr_image_pyramid(vr_ctx* ctx, const float* rgba, int32_t width, int32_
                            float* out, void* stream) {
     if (!ctx) return VR_ERR_INVALID_ARG;
     const int tl = tile_log2(tile);
-    if (!rgba || !out || width <= 0 || height <= 0 || tl == -2)
-        return fail(ctx, VR_ERR_INVALID_ARG, "vr_image_pyramid: need images, positive sizes and tile 0 or a "
+    if (!rgba || !out || width <= 0 || height <= 0 || width > (1 << 20) || height > (1 << 20) || tl == -2)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_image_pyramid: need images, sizes in [1, 2^20] and tile 0 or a "
                                              "power of two in [8, 4096]");
     if ((reinterpret_cast<uintptr_t>(rgba) | reinterpret_cast<uintptr_t>(out)) & 15)
         return fail(ctx, VR_ERR_INVALID_ARG, "vr_image_pyramid: images must be 16-byte aligned");

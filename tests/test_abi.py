@@ -70,7 +70,8 @@ def test_pyramid_layout_matches_the_oracle():
         for tile in (0, 8, 64):
             levels, packed = oracle.pyramid(np.zeros((h, w, 4), np.float32), tile)
             assert vr.vr_pyramid_layout(w, h, tile) == (levels, packed.size)
-    for bad in ((0, 5, 0), (5, 0, 0), (4, 4, 12), (4, 4, 4), (4, 4, 8192)):
+    assert vr.vr_pyramid_layout(1 << 20, 3, 0)[0] == 21  # the largest side accepted
+    for bad in ((0, 5, 0), (5, 0, 0), (4, 4, 12), (4, 4, 4), (4, 4, 8192), ((1 << 20) + 1, 4, 0)):
         with pytest.raises(vr.VrError):
             vr.vr_pyramid_layout(*bad)
 
