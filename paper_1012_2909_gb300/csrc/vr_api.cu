@@ -193,6 +193,8 @@ VolDev vol_dev(const vr_ctx* c) {
     v.pitch = c->pitch;
     v.rows = c->rows;
     v.slot_elems = c->slot_elems;
+    // brick value ranges exist for in-core cubes (the streamed cache has none)
+    v.range_max = (c->minmax && !c->ooc) ? c->minmax + (long long)c->nbx * c->nby * c->nbz : nullptr;
     return v;
 }
 
@@ -713,6 +715,8 @@ TFDev tf_dev(const vr_ctx* ctx) {
     for (int i = 0; i < t.n; ++i) t.tab[i] = ctx->tf[(size_t)i];
     t.vmin = ctx->vmin;
     t.inv_range = 1.0f / (ctx->vmax - ctx->vmin);
+    t.zero_top = -1;
+    while (t.zero_top + 1 < t.n && t.tab[t.zero_top + 1].w == 0.f) ++t.zero_top;
     return t;
 }
 

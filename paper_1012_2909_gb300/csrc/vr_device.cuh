@@ -176,6 +176,7 @@ struct Seg {
     float gx, gy, gz;
     int n;          // samples in this segment
     long long base; // element offset of the slot
+    int brick;      // linear brick id
 };
 
 // Start a segment at sample k: pick the brick holding p_k (any brick whose
@@ -210,7 +211,8 @@ __device__ __forceinline__ bool seg_begin(const Ray& r, int k, const VolDev& v, 
     n = max(n, 1);
     n = min(n, min(cap, r.k1 - k));
     s.n = n;
-    const int slot = v.table[(bz * v.nby + by) * v.nbx + bx];
+    s.brick = (bz * v.nby + by) * v.nbx + bx;
+    const int slot = v.table[s.brick];
     s.base = (long long)slot * v.slot_elems;
     return slot >= 0;
 }
@@ -273,13 +275,34 @@ __device__ __forceinline__ float fetch_trilinear_pair(const T* __restrict__ slot
     return fmaf(fz, b1 - b0, b0);
 }
 
+// True when every sample of brick b is certain to have opacity exactly 0: its
+// stored maximum (which bounds every trilinear sample in it) maps below the
+// transparent nodes 0..zero_top.  Values below the maximum, and NaN, map to
+// lower nodes, and a lookup between two zero-alpha nodes returns 0, so such a
+// segment leaves (C, T) unchanged and can be skipped.
+__device__ __forceinline__ int tf_node(int n, float vmin, float inv_range, float val, float& x);
+__device__ __forceinline__ bool brick_transparent(const VolDev& v, const TFDev& tf, int b) {
+    if (!v.range_max || tf.zero_top < 1) return false;
+    const unsigned int e = v.range_max[b];
+    const float mx = __uint_as_float((e & 0x80000000u) ? (e & 0x7fffffffu) : ~e);
+    float x;
+    return tf_node(tf.n, tf.vmin, tf.inv_range, mx, x) + 1 <= tf.zero_top;
+}
+
+// Table position x of a value and its lower node i (node-centred, clamped):
+// monotone in the value.  A NaN value maps to node 0 with weight 0.
+__device__ __forceinline__ int tf_node(int n, float vmin, float inv_range, float val, float& x) {
+    float u = (val - vmin) * inv_range;
+    u = fminf(fmaxf(u, 0.f), 1.f);
+    x = u * (float)(n - 1);
+    return min((int)x, n - 2);
+}
+
 // Node-centred linear lookup of the table in shared memory, clamped.
 __device__ __forceinline__ float4 tf_lookup(const float4* __restrict__ tab, int n, float vmin,
                                             float inv_range, float val) {
-    float u = (val - vmin) * inv_range;
-    u = fminf(fmaxf(u, 0.f), 1.f);
-    const float x = u * (float)(n - 1);
-    const int i = min((int)x, n - 2);
+    float x;
+    const int i = tf_node(n, vmin, inv_range, val, x);
     const float w = x - (float)i;
     const float4 a = tab[i], b = tab[i + 1];
     return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y),

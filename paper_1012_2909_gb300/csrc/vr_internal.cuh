@@ -37,12 +37,15 @@ struct VolDev {
     int B, log2B;
     int pitch, rows;   // rows = B + 2
     long long slot_elems;
+    const unsigned int* range_max;  // per brick: ordered-int maximum of its stored values
+                                    // (ghost included), or null when unknown
 };
 
 struct TFDev {
     float4 tab[kMaxTF];
     int n;
-    float vmin, inv_range, pad;
+    float vmin, inv_range;
+    int zero_top;  // alpha is 0 at every node 0..zero_top (-1: node 0 is not transparent)
 };
 
 // Float-float camera constants, split on the host from a CamDev.  With sx = px + 1/2,

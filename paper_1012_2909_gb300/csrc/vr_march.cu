@@ -62,6 +62,10 @@ k_march(const __grid_constant__ MarchParams P) {
             while (k < r.k1 && !done) {
                 Seg s;
                 seg_begin(r, k, P.vol, e32, kSegCap, s);
+                if (MODE == VR_COMPOSITE && brick_transparent(P.vol, P.tf, s.brick)) {
+                    k += s.n;  // opacity 0 throughout: (C, T) would not change
+                    continue;
+                }
                 const T* slot = pool + s.base;
                 const T* slot1 = PAIRED ? pool1 + s.base : nullptr;
                 // U samples fetched together (more loads in flight), then

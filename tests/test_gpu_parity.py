@@ -129,6 +129,34 @@ def test_transfer_function_and_termination_extremes(vr, ntf, ert, vrange):
                     gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_transparent_bricks_are_skipped_exactly(vr, storage):
+    """A table that is transparent below 6 sigma: the composite marcher skips every brick
+    whose stored maximum maps below the transparent nodes (noise-only bricks), executes
+    fewer samples than the rays hold, and still equals the oracle."""
+    dims = (80, 72, 96)
+    vol = synth.generate(synth.cube_params(*dims, seed=13, nsrc=6))
+    tf = synth.viridis_ramp_tf()
+    node_v = -1.0 + 21.0 * np.arange(256) / 255.0
+    tf[node_v < 6.0, 3] = 0.0
+    cams = [synth.orbit_view(dims, 35.0, 48, 40), synth.ortho_view(dims, 48, 40)]
+    r = vr.Renderer(0, brick=16)
+    r.load_cube(vol, storage)
+    r.set_transfer_function(tf, -1.0, 20.0)
+    r.set_camera(cams)
+    counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    vr.vr_set_sample_counter(r.ctx, counter)
+    img = r.render("composite").cpu().numpy()
+    vr.vr_set_sample_counter(r.ctx, None)
+    r.close()
+    sc = oracle.Scene(oracle.round_storage(vol, storage), tf, -1.0, 20.0, 0.5, 0.99)
+    total = 0
+    for i, c in enumerate(cams):
+        st = compare(img[i].reshape(-1, 4), sc, c, "composite", tol=1e-4)
+        total += st["nsamples"]
+    assert int(counter.item()) < 0.8 * total, (int(counter.item()), total)
+
+
 def test_fine_step(vr):
     """A step of 0.05 voxel (20 samples per voxel, thousands per ray), every path."""
     dims = (24, 20, 36)
