@@ -196,7 +196,9 @@ vr_status vr_set_camera(vr_ctx* ctx, const vr_camera* cams, int ncams);
  *   t >= 0; trilinear interpolation of voxels centred at integer + 1/2,
  *   clamped to the edge; transfer function as set.
  *   VR_COMPOSITE: C += T a rgb, T *= (1 - a), stop after the sample at which
- *     1 - T >= ert; output (C, 1 - T).
+ *     1 - T >= ert; output (C, 1 - T).  The image-order path skips a brick
+ *     whose stored maximum maps to table nodes of opacity 0 (the image is
+ *     unchanged; its samples are not counted as executed).
  *   VR_MIP: m = max_k v(p_k); output TF(m) (straight), or 0 with no samples.
  * out_max (DEVICE, ncams x height x width float32, may be NULL) receives m
  * in VR_MIP mode (-inf with no samples); it is ignored in VR_COMPOSITE mode.
