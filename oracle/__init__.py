@@ -67,7 +67,8 @@ class OrcScene(ctypes.Structure):
                 ("vol", ctypes.c_void_p), ("tf", ctypes.c_void_p), ("ntf", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double),
                 ("step", ctypes.c_double), ("ert", ctypes.c_double), ("dk0", ctypes.c_int32),
-                ("dk1", ctypes.c_int32)]
+                ("dk1", ctypes.c_int32), ("pos_err", ctypes.c_double), ("dstop", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -88,7 +89,7 @@ def _load():
             lib.orc_render_sortlast.argtypes = [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P,
                                                 _P, ctypes.c_int]
             lib.orc_backward.restype = ctypes.c_int
-            lib.orc_backward.argtypes = [_P, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_int]
+            lib.orc_backward.argtypes = [_P, _P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int]
             lib.orc_touch.restype = ctypes.c_int
             lib.orc_touch.argtypes = [_P, _P, _P, ctypes.c_int64, _P, ctypes.c_int]
             lib.orc_round_bf16.restype = None
@@ -116,19 +117,46 @@ def camera_struct(cam: dict) -> OrcCamera:
     return c
 
 
+U32 = 2.0 ** -24  # unit roundoff of FP32
+
+
+def pos_err_bricked(brick: int, far: float = 0.0) -> float:
+    """Sample-position error bound (voxels, per axis) of a renderer that steps samples in
+    brick-local FP32 coordinates: |g| <= brick + 2 rounded three times (anchor, offset,
+    step FMA), plus the drift of the FP32-rounded step vector over one brick, at most
+    u (brick + 1), plus the float-float anchor's own error for a sample `far` voxels
+    from the origin (2^-40 far)."""
+    return U32 * (4 * brick + 7) + 2.0 ** -40 * far
+
+
+def pos_err_marcher(step: float, far: float = 0.0, span: int = 12) -> float:
+    """Sample-position error bound (voxels, per axis) of a renderer that re-anchors each ray
+    in float-float every `span` samples and steps in FP32 relative to the anchor's voxel:
+    the remainder at the anchor (in [0, 1], one rounding), the stepped coordinate
+    q = q0 + j e (|q| <= 1 + (span - 1) step, one rounding) and the drift of the
+    FP32-rounded step vector over the span (at most u (span - 1) step), plus the
+    float-float anchor's own error for a sample `far` voxels from the origin."""
+    return U32 * (2.0 + 2.0 * (span - 1) * float(step)) + 2.0 ** -40 * far
+
+
 class Scene:
-    """A cube (float32 values as stored), a transfer function and march settings."""
+    """A cube (float32 values as stored), a transfer function and march settings.
+
+    pos_err is the error model behind the ambiguity windows (see oracle.c): a bound on the
+    renderer's sample-position error in voxels per axis.  The default is the bricked
+    stepping bound for 128^3 bricks, the largest brick edge the renderer uses."""
 
     def __init__(self, vol: np.ndarray, tf: np.ndarray, vmin: float, vmax: float,
-                 step: float = 0.5, ert: float = 0.99):
+                 step: float = 0.5, ert: float = 0.99, pos_err: float | None = None):
         vol = np.ascontiguousarray(vol, dtype=np.float32)
         tf = np.ascontiguousarray(tf, dtype=np.float32)
         assert vol.ndim == 3 and tf.ndim == 2 and tf.shape[1] == 4 and tf.shape[0] >= 2
         self.vol, self.tf = vol, tf
         self.nz, self.ny, self.nx = vol.shape
         self.vmin, self.vmax, self.step, self.ert = float(vmin), float(vmax), float(step), float(ert)
+        self.pos_err = pos_err_bricked(128) if pos_err is None else float(pos_err)
 
-    def _struct(self, mode: int, ert=None, dk0=0, dk1=0) -> OrcScene:
+    def _struct(self, mode: int, ert=None, dk0=0, dk1=0, dstop=0) -> OrcScene:
         s = OrcScene()
         s.nx, s.ny, s.nz = self.nx, self.ny, self.nz
         s.vol, s.tf = self.vol.ctypes.data, self.tf.ctypes.data
@@ -136,6 +164,7 @@ class Scene:
         s.vmin, s.vmax, s.step = self.vmin, self.vmax, self.step
         s.ert = self.ert if ert is None else float(ert)
         s.dk0, s.dk1 = int(dk0), int(dk1)
+        s.pos_err, s.dstop = self.pos_err, int(dstop)
         return s
 
 
@@ -144,11 +173,12 @@ def _nthreads(n):
 
 
 def render(scene: Scene, cam: dict, mode: str = "composite", pixels=None, *, ert=None, dk0=0,
-           dk1=0, nthreads=None) -> dict:
-    """Render pixels (flat py*W+px; None = whole image) -> dict(rgba, max, nsamples, flags)."""
+           dk1=0, dstop=0, nthreads=None) -> dict:
+    """Render pixels (flat py*W+px; None = whole image) -> dict(rgba, max, nsamples, flags).
+    dk0, dk1, dstop select an alternative outcome of an ambiguous ray (see variants)."""
     lib = _load()
     m = {"composite": 0, "mip": 1}[mode]
-    s = scene._struct(m, ert, dk0, dk1)
+    s = scene._struct(m, ert, dk0, dk1, dstop)
     c = camera_struct(cam)
     if pixels is None:
         npix = cam["width"] * cam["height"]
@@ -189,8 +219,12 @@ def render_sortlast(scene: Scene, cam: dict, brick: int, mode: str = "composite"
 
 
 def backward(scene: Scene, cams: list, dimg: np.ndarray, mode: str = "composite", *,
-             with_volume=True, ert=None, nthreads=None):
-    """dL/dTF (ntf x 4) and dL/dvol (nz, ny, nx) for dL/dI = dimg (ncams, H, W, 4)."""
+             with_volume=True, ert=None, nthreads=None, ambiguity=False):
+    """dL/dTF (ntf x 4) and dL/dvol (nz, ny, nx) for dL/dI = dimg (ncams, H, W, 4).
+    With ambiguity=True also returns a third array (nz, ny, nx): per voxel, a bound on how
+    far a renderer's voxel gradient may legitimately be from dL/dvol (samples within
+    rounding of a table node or of the MIP maximum, rays whose end sample or termination
+    is within rounding of its threshold)."""
     lib = _load()
     m = {"composite": 0, "mip": 1}[mode]
     s = scene._struct(m, ert)
@@ -198,15 +232,19 @@ def backward(scene: Scene, cams: list, dimg: np.ndarray, mode: str = "composite"
     g = np.ascontiguousarray(dimg, dtype=np.float64)
     assert g.shape == (len(cams), cams[0]["height"], cams[0]["width"], 4)
     dtf = np.zeros((scene.tf.shape[0], 4), np.float64)
+    with_volume = with_volume or ambiguity
     dvol = np.zeros(scene.vol.shape, np.float64) if with_volume else None
+    amb = np.zeros(scene.vol.shape, np.float64) if ambiguity else None
     nt = _nthreads(nthreads)
-    if with_volume:  # one voxel accumulator per thread
-        nt = max(1, min(nt, int(4e9 // max(1, dvol.nbytes))))
+    if with_volume:  # one voxel accumulator (two with the ambiguity bound) per thread
+        per = dvol.nbytes * (2 if ambiguity else 1)
+        nt = max(1, min(nt, int(4e9 // max(1, per))))
     rc = lib.orc_backward(ctypes.byref(s), arr, len(cams), _ptr(g), _ptr(dtf),
-                          None if dvol is None else _ptr(dvol), nt)
+                          None if dvol is None else _ptr(dvol), None if amb is None else _ptr(amb),
+                          nt)
     if rc:
         raise ValueError("orc_backward: bad arguments")
-    return dtf, dvol
+    return (dtf, dvol, amb) if ambiguity else (dtf, dvol)
 
 
 def touched(scene: Scene, cam: dict, mode: str = "mip", pixels=None, nthreads=None) -> np.ndarray:
@@ -295,8 +333,10 @@ def l2_loss(img: np.ndarray, target: np.ndarray):
 
 
 def variants(flags: int):
-    """(ert shift, dk0, dk1) combinations that a flagged ray may legitimately take."""
+    """(dstop, dk0, dk1) combinations that a flagged ray may legitimately take: its first
+    sample one earlier or later (bit 0), its end one earlier or later (bit 1), its
+    termination one sample earlier or later (bit 2)."""
     k0s = (0, -1, 1) if flags & 1 else (0,)
     k1s = (0, -1, 1) if flags & 2 else (0,)
-    es = (0.0, -2e-5, 2e-5) if flags & 4 else (0.0,)
-    return [(e, a, b) for e in es for a in k0s for b in k1s]
+    ds = (0, -1, 1) if flags & 4 else (0,)
+    return [(e, a, b) for e in ds for a in k0s for b in k1s]

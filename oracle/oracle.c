@@ -26,11 +26,23 @@
  *      premultiplied.  MIP: TF(max v) straight, (0,0,0,0) with no samples.
  *   7. adjoint of 6 with respect to the table entries and the voxels.
  *
- * Ambiguous rays (a sample-count decision within rounding of a threshold) are
- * flagged so that a test can accept either outcome:
- *   bit 0: t_near/step within 1e-4 of an integer (first sample in or out)
- *   bit 1: t_far/step within 1e-4 of an integer (last sample in or out)
- *   bit 2: some 1 - T within 1e-5 of ert (termination one sample earlier/later)
+ * Ambiguous rays (a decision that the renderer takes in lower precision lies
+ * within its rounding of the threshold) are flagged so that a test can accept
+ * either outcome.  The windows follow from the renderer's arithmetic, stated
+ * here as an error model (the scene's pos_err and u = 2^-24):
+ *   - each sample position is within pos_err voxels (every axis) of the exact
+ *     one; every FP32 operation rounds to nearest (relative error <= u);
+ *   - the ray set-up is float-float (about 44 bits): a plane crossing
+ *     t = (X - o_a) / d_a is within 2^-43 (|o_a| + n_a + |t|) / |d_a| of the
+ *     exact one, so t/step is within that divided by step; the window used is
+ *     2^7 times wider.
+ * Then (first order, each window twice the bound):
+ *   bit 0: t_near/step within the set-up bound of an integer (first sample in or out)
+ *   bit 1: t_far/step within it (last sample in or out)
+ *   bit 2: some 1 - T within E_k of ert, where E_k bounds the FP32 error of
+ *          1 - T after sample k: E_k = (1 - a_k) E_{k-1} + T_{k-1} da_k + 2 u T_k,
+ *          da_k the alpha error from the sample-value error dv_k (see trilinear)
+ *          through the table slope, plus the FP32 threshold's own rounding.
  */
 #include <math.h>
 #include <pthread.h>
@@ -56,7 +68,13 @@ typedef struct {
     double step;
     double ert;       /* termination threshold on accumulated alpha; > 1 disables */
     int32_t dk0, dk1; /* shifts applied to the first / end sample index (variants) */
+    double pos_err;   /* error model: bound on the renderer's sample-position error, voxels */
+    int32_t dstop;    /* variant: stop |dstop| samples after (> 0) or before (< 0) the
+                         sample at which termination happens; 0 = none */
+    int32_t pad_;
 } orc_scene;
+
+#define U32 5.9604644775390625e-08 /* 2^-24, unit roundoff of FP32 */
 
 #define FLAG_K0 1
 #define FLAG_K1 2
@@ -83,11 +101,14 @@ static void camera_ray(const orc_camera* c, int64_t px, int64_t py, double o[3],
 }
 
 /* ---------------------------------------------------------------- step 2: slab */
+/* Interval [tnear, tfar) of the ray in the box, t >= 0; an_/af_ receive the axis whose
+   plane sets each end (-1: tnear is the t >= 0 clamp). */
 static int box_interval(const orc_scene* s, const double o[3], const double d[3],
-                        double* tnear, double* tfar)
+                        double* tnear, double* tfar, int* an_, int* af_)
 {
     double n[3] = {(double)s->nx, (double)s->ny, (double)s->nz};
     double lo = 0.0, hi = INFINITY;
+    int an = -1, af = -1;
     for (int a = 0; a < 3; ++a) {
         if (d[a] == 0.0) {
             if (o[a] < 0.0 || o[a] > n[a]) return 0;
@@ -96,11 +117,19 @@ static int box_interval(const orc_scene* s, const double o[3], const double d[3]
         double t1 = (0.0 - o[a]) / d[a];
         double t2 = (n[a] - o[a]) / d[a];
         double tl = t1 < t2 ? t1 : t2, th = t1 < t2 ? t2 : t1;
-        if (tl > lo) lo = tl;
-        if (th < hi) hi = th;
+        if (tl > lo) {
+            lo = tl;
+            an = a;
+        }
+        if (th < hi) {
+            hi = th;
+            af = a;
+        }
     }
     *tnear = lo;
     *tfar = hi;
+    if (an_) *an_ = an;
+    if (af_) *af_ = af;
     return lo < hi;
 }
 
@@ -110,8 +139,22 @@ static int64_t clampi(int64_t i, int64_t n)
     return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
 }
 
-/* Value at p plus, optionally, the 8 voxel indices and weights it used. */
-static double trilinear(const orc_scene* s, const double p[3], int64_t idx[8], double w[8])
+static double voxel(const orc_scene* s, int64_t x, int64_t y, int64_t z)
+{
+    return (double)s->vol[(z * s->ny + y) * s->nx + x];
+}
+
+/* Value at p plus, optionally, the 8 voxel indices and weights it used, and a bound
+   dv on how far the renderer's FP32 value of this sample can be from it (error model
+   of the header, first order): moving the position by pos_err on each axis changes
+   the value by at most pos_err * sum_a D_a, D_a the largest difference of neighbouring
+   voxels along axis a around the sample (the cell's edges, taken one cell inwards at a
+   clamped face so that a sample pushed across the face is covered).  The FP32 lerps
+   lerp(f, a, b) = a + f (b - a), three levels (x, y, z), add at each level one
+   rounding of a difference (at most u D_a) and one of a convex combination (at most
+   u M, M the largest |corner|): u (sum_a D_a + 3 M) in all. */
+static double trilinear(const orc_scene* s, const double p[3], int64_t idx[8], double w[8],
+                        double* dv)
 {
     int64_t n[3] = {s->nx, s->ny, s->nz};
     int64_t i0[3], i1[3];
@@ -123,7 +166,7 @@ static double trilinear(const orc_scene* s, const double p[3], int64_t idx[8], d
         i0[a] = clampi((int64_t)fl, n[a]);
         i1[a] = clampi((int64_t)fl + 1, n[a]);
     }
-    double val = 0.0;
+    double val = 0.0, M = 0.0;
     int c = 0;
     for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
@@ -135,9 +178,32 @@ static double trilinear(const orc_scene* s, const double p[3], int64_t idx[8], d
                             (dz ? f[2] : 1.0 - f[2]);
                 int64_t li = (z * s->ny + y) * s->nx + x;
                 val += wt * (double)s->vol[li];
+                if (fabs((double)s->vol[li]) > M) M = fabs((double)s->vol[li]);
                 if (idx) idx[c] = li;
                 if (w) w[c] = wt;
             }
+    if (dv) {
+        double sumD = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            if (n[a] < 2) continue;
+            int64_t j0 = (int64_t)floor(p[a] - 0.5);
+            if (j0 < 0) j0 = 0;
+            if (j0 > n[a] - 2) j0 = n[a] - 2;
+            int b0 = (a + 1) % 3, b1 = (a + 2) % 3;
+            double D = 0.0;
+            for (int e = 0; e < 4; ++e) {
+                int64_t q0[3], q1[3];
+                q0[a] = j0;
+                q1[a] = j0 + 1;
+                q0[b0] = q1[b0] = (e & 1) ? i1[b0] : i0[b0];
+                q0[b1] = q1[b1] = (e & 2) ? i1[b1] : i0[b1];
+                double dd = fabs(voxel(s, q1[0], q1[1], q1[2]) - voxel(s, q0[0], q0[1], q0[2]));
+                if (dd > D) D = dd;
+            }
+            sumD += D;
+        }
+        *dv = s->pos_err * sumD + U32 * (sumD + 3.0 * M);
+    }
     return val;
 }
 
@@ -168,9 +234,66 @@ static void tf_lookup(const orc_scene* s, double v, tf_eval_t* e)
     }
 }
 
+/* Bound on the renderer's alpha error for a sample of value v whose FP32 value is
+   within dv of v: the steepest alpha slope among the table segments that a value in
+   [v - dv, v + dv] can reach, times dv, plus the rounding of the table position
+   x = (v - vmin) (1 / (vmax - vmin)) (n - 1) (four roundings: at most 4 u (|x| + 1)
+   in segment units) and of the lerp (2 u max alpha). */
+static double alpha_err(const orc_scene* s, double v, double dv)
+{
+    double scale = (double)(s->ntf - 1) / (s->vmax - s->vmin);
+    double x = (v - s->vmin) * scale;
+    double xr = dv * scale + 4.0 * U32 * (fabs(x) + 1.0);
+    double jlo = floor(x - xr), jhi = floor(x + xr);
+    if (jlo < 0.0) jlo = 0.0;
+    if (jhi > (double)(s->ntf - 2)) jhi = (double)(s->ntf - 2);
+    double smax = 0.0, amax = 0.0;
+    for (int64_t j = (int64_t)jlo; j <= (int64_t)jhi; ++j) {
+        double a0 = s->tf[4 * j + 3], a1 = s->tf[4 * (j + 1) + 3];
+        if (fabs(a1 - a0) > smax) smax = fabs(a1 - a0);
+        if (fabs(a0) > amax) amax = fabs(a0);
+        if (fabs(a1) > amax) amax = fabs(a1);
+    }
+    if (x + xr < 0.0 || x - xr > (double)(s->ntf - 1)) smax = 0.0; /* clamped: constant */
+    if (jlo > jhi) { /* reach entirely outside the table: the clamped end entry */
+        int64_t j = x < 0.0 ? 0 : s->ntf - 1;
+        amax = fabs(s->tf[4 * j + 3]);
+    }
+    return smax * xr + 2.0 * U32 * amax;
+}
+
+/* A sample whose table position is within the renderer's rounding (twice the bound
+   from a value error dv) of a node may take the slope of the segment on the other side
+   (reading R14; at the end nodes the other side is the clamped region, slope 0).
+   Returns |sum_c g_c (s_left_c - s_right_c)| for such a sample, else 0. */
+static double node_alt(const orc_scene* s, double v, double dv, const double g[4])
+{
+    double scale = (double)(s->ntf - 1) / (s->vmax - s->vmin);
+    double x = (v - s->vmin) * scale;
+    double xr = 2.0 * (dv * scale + 4.0 * U32 * (fabs(x) + 1.0));
+    double j = nearbyint(x);
+    if (fabs(x - j) > xr || j < 0.0 || j > (double)(s->ntf - 1)) return 0.0;
+    int64_t jn = (int64_t)j;
+    double acc = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        double sl = jn > 0 ? (s->tf[4 * jn + c] - s->tf[4 * (jn - 1) + c]) * scale : 0.0;
+        double sr = jn < s->ntf - 1 ? (s->tf[4 * (jn + 1) + c] - s->tf[4 * jn + c]) * scale : 0.0;
+        acc += g[c] * (sl - sr);
+    }
+    return fabs(acc);
+}
+
 static double frac_dist(double x)
 {
     return fabs(x - nearbyint(x));
+}
+
+/* Window of t/step at a slab end set by axis a: twice 2^6 times the float-float
+   set-up bound 2^-43 (|o_a| + n_a + |t|) / |d_a| of the header, over step. */
+static double end_window(const orc_scene* s, const double o[3], const double d[3], int a, double t)
+{
+    double n[3] = {(double)s->nx, (double)s->ny, (double)s->nz};
+    return ldexp(1.0, -36) * (fabs(o[a]) + n[a] + fabs(t)) / (fabs(d[a]) * s->step);
 }
 
 /* Sample index range [k0, k1) of a ray and its ambiguity flags. */
@@ -178,11 +301,12 @@ static int ray_samples(const orc_scene* s, const double o[3], const double d[3],
                        int64_t* k0, int64_t* k1, int* flags)
 {
     double tn, tf;
+    int an, af;
     *k0 = *k1 = 0;
-    if (!box_interval(s, o, d, &tn, &tf)) return 0;
+    if (!box_interval(s, o, d, &tn, &tf, &an, &af)) return 0;
     double a = tn / s->step, b = tf / s->step;
-    if (tn > 0.0 && frac_dist(a) < 1e-4) *flags |= FLAG_K0;
-    if (frac_dist(b) < 1e-4) *flags |= FLAG_K1;
+    if (an >= 0 && tn > 0.0 && frac_dist(a) <= end_window(s, o, d, an, tn)) *flags |= FLAG_K0;
+    if (af >= 0 && frac_dist(b) <= end_window(s, o, d, af, tf)) *flags |= FLAG_K1;
     *k0 = (int64_t)ceil(a) + s->dk0;
     *k1 = (int64_t)ceil(b) + s->dk1;
     if (*k0 < 0) *k0 = 0;
@@ -206,11 +330,24 @@ static void trace(const orc_scene* s, const orc_camera* cam, int64_t px, int64_t
     r->vmax = -INFINITY;
     camera_ray(cam, px, py, o, d);
     if (!ray_samples(s, o, d, &k0, &k1, &r->flags)) return;
-    double C[3] = {0, 0, 0}, T = 1.0, m = -INFINITY;
+    const int ert_on = s->mode == 0 && s->ert <= 1.0;
+    int64_t nstop = -1; /* variant: execute exactly this many samples */
+    if (ert_on && s->dstop != 0) {
+        orc_scene s0 = *s;
+        s0.dstop = 0;
+        ray_result r0;
+        trace(&s0, cam, px, py, &r0);
+        nstop = r0.nsamp + s->dstop;
+        if (nstop < 1) nstop = 1;
+    }
+    /* the renderer tests 1 - T >= ert with ert and 1 - T rounded to FP32 */
+    const double ert_win = fabs(s->ert - (double)(float)s->ert) + 2.0 * U32;
+    double C[3] = {0, 0, 0}, T = 1.0, m = -INFINITY, E = 0.0;
     for (int64_t k = k0; k < k1; ++k) {
         double t = (double)k * s->step;
         double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
-        double v = trilinear(s, p, NULL, NULL);
+        double dv;
+        double v = trilinear(s, p, NULL, NULL, &dv);
         r->nsamp++;
         if (s->mode == 1) {
             if (v > m) m = v;
@@ -220,9 +357,15 @@ static void trace(const orc_scene* s, const orc_camera* cam, int64_t px, int64_t
         tf_lookup(s, v, &e);
         double a = e.rgba[3];
         for (int c = 0; c < 3; ++c) C[c] += T * a * e.rgba[c];
-        T *= (1.0 - a);
-        if (s->ert <= 1.0 && fabs((1.0 - T) - s->ert) < 1e-5) r->flags |= FLAG_ERT;
-        if (s->ert <= 1.0 && 1.0 - T >= s->ert) break;
+        double Tn = T * (1.0 - a);
+        E = fabs(1.0 - a) * E + T * alpha_err(s, v, dv) + 2.0 * U32 * fabs(Tn);
+        T = Tn;
+        if (nstop >= 0) {
+            if (r->nsamp == nstop) break;
+            continue;
+        }
+        if (ert_on && fabs((1.0 - T) - s->ert) <= 2.0 * E + ert_win) r->flags |= FLAG_ERT;
+        if (ert_on && 1.0 - T >= s->ert) break;
     }
     if (s->mode == 1) {
         r->vmax = m;
@@ -392,7 +535,7 @@ static void trace_sortlast(const orc_scene* s, const orc_camera* cam, int64_t B,
             q->T = 1.0;
             q->m = -INFINITY;
         }
-        double v = trilinear(s, p, NULL, NULL);
+        double v = trilinear(s, p, NULL, NULL, NULL);
         r->nsamp++;
         if (v > q->m) q->m = v;
         if (s->mode == 0) {
@@ -439,84 +582,111 @@ int orc_render_sortlast(const orc_scene* s, const orc_camera* cam, int64_t brick
 
 /* ------------------------------------------------------------- step 7: adjoint */
 typedef struct {
+    int64_t k;        /* sample index */
     double T;         /* transmittance before the sample */
     double a, rgb[3];
+    double v, dv;     /* value, and the bound on the renderer's error in it */
     tf_eval_t e;
     int64_t idx[8];
     double w[8];
 } rec_t;
 
+/* Per-ray scratch of the adjoint: the executed samples of the ray and of one variant,
+   and dL/dv per sample for both. */
 typedef struct {
-    const orc_scene* s;
-    const orc_camera* cams;
-    int32_t ncams;
-    const double* dimg; /* ncams x H x W x 4 */
-    int64_t next;
-    pthread_mutex_t mu;
-    /* per-thread accumulators, merged under the mutex at the end */
-    double* dtf;   /* ntf x 4 */
-    double* dvol;  /* nx*ny*nz or NULL */
-    int64_t total;
-} grad_job;
+    rec_t* buf[2];
+    double* dvs[2];
+    double* alt;
+    int64_t cap[2];
+} ray_work;
 
-static void ray_backward(const orc_scene* s, const orc_camera* cam, int64_t px, int64_t py,
-                         const double g[4], double* dtf, double* dvol, rec_t** buf,
-                         int64_t* cap)
+static void work_reserve(ray_work* w, int b, int64_t n)
 {
-    double o[3], d[3];
-    int64_t k0, k1;
-    int flags = 0;
-    camera_ray(cam, px, py, o, d);
-    if (!ray_samples(s, o, d, &k0, &k1, &flags)) return;
-    /* forward, recording every executed sample */
+    if (n <= w->cap[b]) return;
+    int64_t c = w->cap[b] ? w->cap[b] : 256;
+    while (c < n) c *= 2;
+    w->buf[b] = (rec_t*)realloc(w->buf[b], sizeof(rec_t) * (size_t)c);
+    w->dvs[b] = (double*)realloc(w->dvs[b], sizeof(double) * (size_t)c);
+    if (b == 0) w->alt = (double*)realloc(w->alt, sizeof(double) * (size_t)c);
+    w->cap[b] = c;
+}
+
+/* Forward march of samples k0 .. k1-1 recording each executed one: composite stops
+   after the sample at which 1 - T >= ert, or after exactly nstop samples when
+   nstop >= 0; MIP records every sample.  Returns the number recorded. */
+static int64_t fwd_records(const orc_scene* s, const double o[3], const double d[3], int64_t k0,
+                           int64_t k1, int64_t nstop, ray_work* w, int b)
+{
     int64_t n = 0;
     double T = 1.0;
-    double m = -INFINITY;
-    int64_t kmax = -1;
     for (int64_t k = k0; k < k1; ++k) {
-        if (n == *cap) {
-            *cap = *cap ? 2 * *cap : 256;
-            *buf = (rec_t*)realloc(*buf, sizeof(rec_t) * (size_t)*cap);
-        }
-        rec_t* q = &(*buf)[n++];
+        work_reserve(w, b, n + 1);
+        rec_t* q = &w->buf[b][n++];
         double t = (double)k * s->step;
         double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
-        double v = trilinear(s, p, q->idx, q->w);
-        if (s->mode == 1) {
-            if (v > m) {
-                m = v;
-                kmax = n - 1;
-            }
-            continue;
-        }
-        tf_lookup(s, v, &q->e);
+        q->k = k;
+        q->v = trilinear(s, p, q->idx, q->w, &q->dv);
+        tf_lookup(s, q->v, &q->e);
+        if (s->mode == 1) continue;
         q->T = T;
         q->a = q->e.rgba[3];
         for (int c = 0; c < 3; ++c) q->rgb[c] = q->e.rgba[c];
         T *= (1.0 - q->a);
-        if (s->ert <= 1.0 && 1.0 - T >= s->ert) break;
+        if (nstop >= 0) {
+            if (n == nstop) break;
+        } else if (s->ert <= 1.0 && 1.0 - T >= s->ert) {
+            break;
+        }
+    }
+    return n;
+}
+
+/* Index of the first sample attaining the maximum value (MIP), -1 with no samples. */
+static int64_t first_max(const rec_t* q, int64_t n)
+{
+    int64_t km = -1;
+    double m = -INFINITY;
+    for (int64_t k = 0; k < n; ++k)
+        if (q[k].v > m) {
+            m = q[k].v;
+            km = k;
+        }
+    return km;
+}
+
+/* Reverse sweep over the n recorded samples for dL/dI = g: dL/dv of each sample into
+   dvs, the table gradient added to dtf (when not NULL), and into alt (when not NULL)
+   the node alternative of each sample (node_alt: how much dL/dv changes if the table
+   slope of the other side of a nearby node is taken). */
+static void rev_sweep(const orc_scene* s, const rec_t* buf, int64_t n, const double g[4],
+                      double* dtf, double* dvs, double* alt)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        dvs[k] = 0.0;
+        if (alt) alt[k] = 0.0;
     }
     if (s->mode == 1) {
         /* I = TF(max v): the gradient reaches the first maximal sample only */
-        if (kmax < 0) return;
-        rec_t* q = &(*buf)[kmax];
-        tf_eval_t e;
-        tf_lookup(s, m, &e);
+        int64_t km = first_max(buf, n);
+        if (km < 0) return;
+        const tf_eval_t* e = &buf[km].e;
         double dv = 0.0;
         for (int c = 0; c < 4; ++c) {
-            dtf[4 * e.i + c] += (1.0 - e.w) * g[c];
-            dtf[4 * (e.i + 1) + c] += e.w * g[c];
-            dv += g[c] * e.slope[c];
+            if (dtf) {
+                dtf[4 * e->i + c] += (1.0 - e->w) * g[c];
+                dtf[4 * (e->i + 1) + c] += e->w * g[c];
+            }
+            dv += g[c] * e->slope[c];
         }
-        if (dvol)
-            for (int c = 0; c < 8; ++c) dvol[q->idx[c]] += q->w[c] * dv;
+        dvs[km] = dv;
+        if (alt) alt[km] = node_alt(s, buf[km].v, buf[km].dv, g);
         return;
     }
-    /* reverse sweep: R = colour composited behind the sample (starting from T = 1),
+    /* R = colour composited behind the sample (starting from T = 1),
        P = transmittance behind the sample */
     double R[3] = {0, 0, 0}, P = 1.0;
     for (int64_t k = n - 1; k >= 0; --k) {
-        rec_t* q = &(*buf)[k];
+        const rec_t* q = &buf[k];
         double ga = g[3] * q->T * P;
         double gc[3];
         for (int c = 0; c < 3; ++c) {
@@ -528,14 +698,114 @@ static void ray_backward(const orc_scene* s, const orc_camera* cam, int64_t px, 
         double gch[4] = {gc[0], gc[1], gc[2], ga};
         double dv = 0.0;
         for (int c = 0; c < 4; ++c) {
-            dtf[4 * q->e.i + c] += (1.0 - q->e.w) * gch[c];
-            dtf[4 * (q->e.i + 1) + c] += q->e.w * gch[c];
+            if (dtf) {
+                dtf[4 * q->e.i + c] += (1.0 - q->e.w) * gch[c];
+                dtf[4 * (q->e.i + 1) + c] += q->e.w * gch[c];
+            }
             dv += gch[c] * q->e.slope[c];
         }
-        if (dvol)
-            for (int c = 0; c < 8; ++c) dvol[q->idx[c]] += q->w[c] * dv;
+        dvs[k] = dv;
+        if (alt) alt[k] = node_alt(s, q->v, q->dv, gch);
     }
 }
+
+static void add_amb(double* amb, const rec_t* q, double x)
+{
+    for (int c = 0; c < 8; ++c) amb[q->idx[c]] += q->w[c] * x;
+}
+
+/* Adjoint of one ray.  With amb, also a per-voxel bound on how far the renderer may
+   legitimately be from dvol (readings R11, R14, R15): for every sample near a table
+   node, its node alternative; for MIP, every sample whose value is within the
+   renderer's rounding of the maximum (either may be the first maximal one); for a
+   flagged ray (an end sample or the termination within rounding), the difference of
+   each sample's dL/dv between the ray and each alternative outcome. */
+static void ray_backward(const orc_scene* s, const orc_camera* cam, int64_t px, int64_t py,
+                         const double g[4], double* dtf, double* dvol, double* amb, ray_work* w)
+{
+    double o[3], d[3];
+    int64_t k0, k1;
+    int flags = 0;
+    camera_ray(cam, px, py, o, d);
+    if (!ray_samples(s, o, d, &k0, &k1, &flags)) return;
+    int64_t n = fwd_records(s, o, d, k0, k1, -1, w, 0);
+    rev_sweep(s, w->buf[0], n, g, dtf, w->dvs[0], amb ? w->alt : NULL);
+    if (dvol)
+        for (int64_t k = 0; k < n; ++k)
+            for (int c = 0; c < 8; ++c) dvol[w->buf[0][k].idx[c]] += w->buf[0][k].w[c] * w->dvs[0][k];
+    if (!amb) return;
+    for (int64_t k = 0; k < n; ++k)
+        if (w->alt[k] > 0.0) add_amb(amb, &w->buf[0][k], w->alt[k]);
+    if (s->mode == 1) {
+        int64_t km = first_max(w->buf[0], n);
+        if (km >= 0) {
+            const rec_t* qm = &w->buf[0][km];
+            double gm = fabs(w->dvs[0][km]);
+            int tie = 0;
+            for (int64_t k = 0; k < n; ++k)
+                if (k != km && w->buf[0][k].v >= qm->v - 2.0 * (w->buf[0][k].dv + qm->dv)) {
+                    add_amb(amb, &w->buf[0][k], gm);
+                    tie = 1;
+                }
+            if (tie) add_amb(amb, qm, gm);
+        }
+    }
+    ray_result rr;
+    trace(s, cam, px, py, &rr);
+    if (!rr.flags) return;
+    const int dk0s[3] = {0, -1, 1}, dk1s[3] = {0, -1, 1}, dss[3] = {0, -1, 1};
+    int nk0 = (rr.flags & FLAG_K0) ? 3 : 1, nk1 = (rr.flags & FLAG_K1) ? 3 : 1;
+    int nds = (rr.flags & FLAG_ERT) ? 3 : 1;
+    for (int i0 = 0; i0 < nk0; ++i0)
+        for (int i1 = 0; i1 < nk1; ++i1)
+            for (int id = 0; id < nds; ++id) {
+                if (i0 == 0 && i1 == 0 && id == 0) continue;
+                int64_t a0 = k0 + dk0s[i0], a1 = k1 + dk1s[i1];
+                if (a0 < 0) a0 = 0;
+                int64_t nv = 0;
+                if (a1 > a0) {
+                    int64_t nstop = -1;
+                    if (dss[id] != 0) {
+                        nstop = fwd_records(s, o, d, a0, a1, -1, w, 1) + dss[id];
+                        if (nstop < 1) nstop = 1;
+                    }
+                    nv = fwd_records(s, o, d, a0, a1, nstop, w, 1);
+                    work_reserve(w, 1, nv + 1);
+                    rev_sweep(s, w->buf[1], nv, g, NULL, w->dvs[1], NULL);
+                }
+                /* both lists are in ascending sample index: merge, missing = 0 */
+                int64_t i = 0, j = 0;
+                while (i < n || j < nv) {
+                    int64_t ki = i < n ? w->buf[0][i].k : INT64_MAX;
+                    int64_t kj = j < nv ? w->buf[1][j].k : INT64_MAX;
+                    if (ki == kj) {
+                        add_amb(amb, &w->buf[0][i], fabs(w->dvs[1][j] - w->dvs[0][i]));
+                        ++i;
+                        ++j;
+                    } else if (ki < kj) {
+                        add_amb(amb, &w->buf[0][i], fabs(w->dvs[0][i]));
+                        ++i;
+                    } else {
+                        add_amb(amb, &w->buf[1][j], fabs(w->dvs[1][j]));
+                        ++j;
+                    }
+                }
+            }
+}
+
+typedef struct {
+    const orc_scene* s;
+    const orc_camera* cams;
+    int32_t ncams;
+    const double* dimg; /* ncams x H x W x 4 */
+    int64_t next;
+    pthread_mutex_t mu;
+    /* per-thread accumulators, merged under the mutex at the end */
+    double* dtf;   /* ntf x 4 */
+    double* dvol;  /* nx*ny*nz or NULL */
+    double* amb;   /* nx*ny*nz or NULL */
+    int64_t total;
+} grad_job;
 
 static void* grad_worker(void* arg)
 {
@@ -544,8 +814,9 @@ static void* grad_worker(void* arg)
     int64_t nvox = s->nx * s->ny * s->nz;
     double* dtf = (double*)calloc((size_t)s->ntf * 4, sizeof(double));
     double* dvol = j->dvol ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
-    rec_t* buf = NULL;
-    int64_t cap = 0;
+    double* amb = j->amb ? (double*)calloc((size_t)nvox, sizeof(double)) : NULL;
+    ray_work w;
+    memset(&w, 0, sizeof(w));
     const int64_t chunk = 64;
     for (;;) {
         pthread_mutex_lock(&j->mu);
@@ -560,34 +831,45 @@ static void* grad_worker(void* arg)
             int64_t ci = i / (W * H), r = i % (W * H);
             const double* g = j->dimg + 4 * i;
             if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0 && g[3] == 0.0) continue;
-            ray_backward(s, &j->cams[ci], r % W, r / W, g, dtf, dvol, &buf, &cap);
+            ray_backward(s, &j->cams[ci], r % W, r / W, g, dtf, dvol, amb, &w);
         }
     }
     pthread_mutex_lock(&j->mu);
     for (int64_t i = 0; i < (int64_t)s->ntf * 4; ++i) j->dtf[i] += dtf[i];
     if (dvol)
         for (int64_t i = 0; i < nvox; ++i) j->dvol[i] += dvol[i];
+    if (amb)
+        for (int64_t i = 0; i < nvox; ++i) j->amb[i] += amb[i];
     pthread_mutex_unlock(&j->mu);
     free(dtf);
     free(dvol);
-    free(buf);
+    free(amb);
+    for (int b = 0; b < 2; ++b) {
+        free(w.buf[b]);
+        free(w.dvs[b]);
+    }
+    free(w.alt);
     return NULL;
 }
 
 /*
  * Gradient of a loss with respect to the table (out_dtf, ntf x 4) and the
  * voxels (out_dvol, nx*ny*nz, may be NULL), given dL/dI (ncams x H x W x 4)
- * for the images of the composite (or MIP) renders of the cameras.  Both
- * outputs are overwritten.  Each thread holds its own voxel accumulator.
+ * for the images of the composite (or MIP) renders of the cameras.  out_amb
+ * (nx*ny*nz, may be NULL) receives the per-voxel bound of ray_backward on the
+ * legitimate deviation of a renderer's voxel gradient.  All outputs are
+ * overwritten.  Each thread holds its own voxel accumulators.
  */
 int orc_backward(const orc_scene* s, const orc_camera* cams, int32_t ncams, const double* dimg,
-                 double* out_dtf, double* out_dvol, int nthreads)
+                 double* out_dtf, double* out_dvol, double* out_amb, int nthreads)
 {
     if (!scene_ok(s) || !cams || ncams <= 0 || !dimg || !out_dtf) return -1;
     for (int i = 1; i < ncams; ++i)
         if (cams[i].width != cams[0].width || cams[i].height != cams[0].height) return -1;
+    int64_t nvox = s->nx * s->ny * s->nz;
     memset(out_dtf, 0, sizeof(double) * (size_t)s->ntf * 4);
-    if (out_dvol) memset(out_dvol, 0, sizeof(double) * (size_t)(s->nx * s->ny * s->nz));
+    if (out_dvol) memset(out_dvol, 0, sizeof(double) * (size_t)nvox);
+    if (out_amb) memset(out_amb, 0, sizeof(double) * (size_t)nvox);
     grad_job j;
     memset(&j, 0, sizeof(j));
     j.s = s;
@@ -598,6 +880,7 @@ int orc_backward(const orc_scene* s, const orc_camera* cams, int32_t ncams, cons
     pthread_mutex_init(&j.mu, NULL);
     j.dtf = out_dtf;
     j.dvol = out_dvol;
+    j.amb = out_amb;
     j.total = (int64_t)ncams * cams[0].width * cams[0].height;
     run_threads(grad_worker, &j, nthreads);
     pthread_mutex_destroy(&j.mu);
@@ -641,7 +924,7 @@ static void* touch_worker(void* arg)
                 double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
                 int64_t idx[8];
                 double w[8];
-                double v = trilinear(s, p, idx, w);
+                double v = trilinear(s, p, idx, w, NULL);
                 for (int c = 0; c < 8; ++c) __atomic_store_n(&j->mask[idx[c]], 1, __ATOMIC_RELAXED);
                 if (s->mode == 0) {
                     tf_eval_t e;

@@ -21,11 +21,23 @@ MUTANTS = {
     "axes swapped in the index": ("int64_t li = (z * s->ny + y) * s->nx + x;",
                                   "int64_t li = (y * s->nz + z) * s->nx + x;"),
     "termination before the crossing sample": (
-        "        for (int c = 0; c < 3; ++c) C[c] += T * a * e.rgba[c];\n        T *= (1.0 - a);\n"
-        "        if (s->ert <= 1.0 && fabs((1.0 - T) - s->ert) < 1e-5) r->flags |= FLAG_ERT;\n"
-        "        if (s->ert <= 1.0 && 1.0 - T >= s->ert) break;",
-        "        if (s->ert <= 1.0 && 1.0 - T * (1.0 - a) >= s->ert) break;\n"
-        "        for (int c = 0; c < 3; ++c) C[c] += T * a * e.rgba[c];\n        T *= (1.0 - a);"),
+        "        if (ert_on && 1.0 - T >= s->ert) break;",
+        "        if (ert_on && 1.0 - T * (1.0 - a) >= s->ert) break;"),
+    "termination window widened 100x": ("fabs((1.0 - T) - s->ert) <= 2.0 * E + ert_win",
+                                         "fabs((1.0 - T) - s->ert) <= 200.0 * E + 100.0 * ert_win"),
+    "termination flag dropped": ("if (ert_on && fabs((1.0 - T) - s->ert) <= 2.0 * E + ert_win) r->flags |= FLAG_ERT;",
+                                 ""),
+    "termination window ignores the position error": ("*dv = s->pos_err * sumD + U32 * (sumD + 3.0 * M);",
+                                                      "*dv = U32 * (sumD + 3.0 * M);"),
+    "end-sample window widened 100x": ("return ldexp(1.0, -36) * (fabs(o[a]) + n[a] + fabs(t)) / (fabs(d[a]) * s->step);",
+                                       "return ldexp(100.0, -36) * (fabs(o[a]) + n[a] + fabs(t)) / (fabs(d[a]) * s->step);"),
+    "first-sample flag dropped": ("if (an >= 0 && tn > 0.0 && frac_dist(a) <= end_window(s, o, d, an, tn)) *flags |= FLAG_K0;",
+                                  ""),
+    "last-sample flag dropped": ("if (af >= 0 && frac_dist(b) <= end_window(s, o, d, af, tf)) *flags |= FLAG_K1;", ""),
+    "termination variant not shifted": ("nstop = r0.nsamp + s->dstop;", "nstop = r0.nsamp;"),
+    "adjoint node alternative dropped": ("    if (fabs(x - j) > xr || j < 0.0 || j > (double)(s->ntf - 1)) return 0.0;",
+                                         "    return 0.0;"),
+    "adjoint flagged rays not bounded": ("    if (!rr.flags) return;", "    return;"),
     "perspective direction not normalised": ("for (int a = 0; a < 3; ++a) d[a] = dd[a] / len;",
                                              "for (int a = 0; a < 3; ++a) d[a] = dd[a];"),
     "pixel corner instead of centre": ("double u = l + ((double)px + 0.5) * (r - l) / (double)c->width;",
@@ -36,7 +48,7 @@ MUTANTS = {
     "mip keeps the minimum": ("            if (v > m) m = v;\n            continue;", "            if (!(v > m) || m == -INFINITY) m = v;\n            continue;"),
     "slab starts behind the eye": [("double lo = 0.0, hi = INFINITY;", "double lo = -INFINITY, hi = INFINITY;"),
                                    ("    if (*k0 < 0) *k0 = 0;\n", "")],
-    "slab exit takes the farther plane": ("if (th < hi) hi = th;", "if (th > hi || hi == INFINITY) hi = th;"),
+    "slab exit takes the farther plane": ("        if (th < hi) {", "        if (th > hi || hi == INFINITY) {"),
     "sort-last folds back to front": ("if (x->key != y->key) return x->key < y->key ? -1 : 1;",
                                       "if (x->key != y->key) return x->key < y->key ? 1 : -1;"),
     "sort-last orthographic key sign": ("q->key += d[a] > 0 ? b[a] : (d[a] < 0 ? -b[a] : 0);",
@@ -47,7 +59,7 @@ MUTANTS = {
                                      "for (int c = 0; c < 4; ++c) __atomic_store_n"),
     "bf16 truncates": ("u = (u + 0x7fffu + lsb) & 0xffff0000u;", "u = u & 0xffff0000u;"),
     "bf16 ties away from zero": ("u = (u + 0x7fffu + lsb) & 0xffff0000u;", "u = (u + 0x8000u) & 0xffff0000u;"),
-    "mip adjoint tf weight swapped": ("dtf[4 * e.i + c] += (1.0 - e.w) * g[c];", "dtf[4 * e.i + c] += e.w * g[c];"),
+    "mip adjoint tf weight swapped": ("dtf[4 * e->i + c] += (1.0 - e->w) * g[c];", "dtf[4 * e->i + c] += e->w * g[c];"),
     "adjoint suffix transmittance kept at one": ("        P *= (1.0 - q->a);\n", ""),
     "adjoint colour gradient without opacity": ("gc[c] = g[c] * q->T * q->a;", "gc[c] = g[c] * q->T;"),
     "tf slope where the lookup is clamped": (

@@ -459,3 +459,126 @@ def test_overlay_box_behind_the_camera_draws_nothing():
     _, key = oracle.overlay(np.zeros((32, 32, 4)), c, np.array([[-2, -2, -9, 2, 2, -3]]),
                             np.ones((1, 4), np.float32))
     assert not key.any()
+
+
+# ------------------------------------------------------- ambiguity windows (reading R11)
+# The windows are derived from the renderer's FP32 arithmetic (oracle.c header).  For a
+# constant cube and a constant table the value has no position error and the alpha only
+# lerp rounding, so the termination window is a few 1e-7: a ray whose 1 - (1-a)^n lands
+# 1e-9 from the threshold must be flagged, one landing 3e-6 away must not.
+def _const_ray(a, nz=60):
+    vol = np.full((nz, 3, 3), 2.0, np.float32)
+    tf = np.tile(np.array([0.3, 0.6, 0.2, a], np.float32), (4, 1))
+    c = cam(0, (1.5, 1.5, -1.3), (0, 0, 1))  # t in [1.3, 61.3): k = 3 .. 122 at step 0.5
+    return vol, tf, c
+
+
+@pytest.mark.parametrize("delta,flagged", [(1e-9, True), (3e-6, False)])
+def test_termination_window_constant_cube(delta, flagged):
+    a = float(np.float32(0.1))
+    vol, tf, c = _const_ray(a)
+    n = 44  # 1 - 0.9^44 = 0.9903
+    A = 1 - (1 - a) ** n
+    sc = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5, ert=A - delta, pos_err=oracle.pos_err_marcher(0.5))
+    r = oracle.render(sc, c, "composite")
+    assert r["nsamples"][0] == n
+    assert bool(r["flags"][0] & 4) == flagged
+    assert not r["flags"][0] & 3
+
+
+def test_termination_variants_stop_one_sample_apart():
+    a = float(np.float32(0.1))
+    vol, tf, c = _const_ray(a)
+    n = 44
+    sc = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5, ert=1 - (1 - a) ** n - 1e-12)
+    for ds in (-1, 0, 1):
+        r = oracle.render(sc, c, "composite", dstop=ds)
+        assert r["nsamples"][0] == n + ds
+        np.testing.assert_allclose(r["rgba"][0, 3], 1 - (1 - a) ** (n + ds), atol=TOL)
+    assert sorted(oracle.variants(4)) == [(-1, 0, 0), (0, 0, 0), (1, 0, 0)]
+
+
+def test_termination_window_scales_with_position_error():
+    """A cube that ramps along the ray (1 per voxel) under a linear alpha table: the value
+    error is pos_err per voxel of displacement, so a ray 1e-6 from the threshold is flagged
+    with a 1e-4 voxel position error and not without one; 1e-4 away it is never flagged."""
+    nz = 80
+    vol = np.broadcast_to(np.arange(nz, dtype=np.float32)[:, None, None] * 0.25, (nz, 3, 3)).copy()
+    tf = synth.viridis_ramp_tf()
+    c = cam(0, (1.5, 1.5, -0.7), (0, 0, 1))
+    base = oracle.Scene(vol, tf, -1.0, 20.0, step=0.5, ert=2.0)
+    r = oracle.render(base, c, "composite")
+    # accumulated alpha after each sample from the exact render with no termination
+    alphas = [oracle.render(base, c, "composite", ert=2.0, dk1=-(int(r["nsamples"][0]) - j))["rgba"][0, 3]
+              for j in range(1, int(r["nsamples"][0]) + 1)]
+    n = next(j for j, A in enumerate(alphas, 1) if A > 0.9)
+    A = alphas[n - 1]
+    for pe, delta, flagged in ((1e-4, 1e-6, True), (0.0, 1e-6, False), (1e-4, 1e-4, False)):
+        sc = oracle.Scene(vol, tf, -1.0, 20.0, step=0.5, ert=A - delta, pos_err=pe)
+        out = oracle.render(sc, c, "composite")
+        assert out["nsamples"][0] == n
+        assert bool(out["flags"][0] & 4) == flagged, (pe, delta)
+
+
+@pytest.mark.parametrize("end,delta,flagged", [(0, 1e-12, True), (0, 1e-8, False),
+                                               (1, 1e-12, True), (1, 1e-8, False)])
+def test_end_sample_window(end, delta, flagged):
+    """t_near/step (end 0) or t_far/step (end 1) within 1e-12 of an integer is flagged; 1e-8
+    away is beyond the float-float set-up bound (2^-43 (|o| + n + t) / (|d| step), about
+    5e-12 here, windowed at 2^7 times that) and is not."""
+    vol = np.full((10, 3, 3), 2.0, np.float32)
+    tf = synth.viridis_ramp_tf(8)
+    # orthographic along +z from z0: t_near = -z0, t_far = 10 - z0; step 0.3 (the two ends'
+    # fractions then differ by 1/3)
+    z0 = -0.3 * (5 + delta) if end == 0 else 10 - 0.3 * (40 + delta)
+    sc = oracle.Scene(vol, tf, 0.0, 10.0, step=0.3, ert=2.0)
+    r = oracle.render(sc, cam(0, (1.5, 1.5, z0), (0, 0, 1)), "mip")
+    bit = 1 << end
+    assert bool(r["flags"][0] & bit) == flagged
+    assert not r["flags"][0] & (3 ^ bit)
+
+
+# ----------------------------------------- adjoint: bound on legitimate deviations (R14)
+def test_adjoint_node_alternative_bound():
+    """Every sample of a constant cube sits exactly on a table node: the voxel gradient may
+    take either one-sided slope.  The ambiguity bound must cover the gradient computed with
+    the other side's slope (a table whose segment right of the node continues the left
+    slope), and is zero for a value between nodes."""
+    vol = np.full((12, 4, 4), 7.0, np.float32)   # node 7 of 11 over [0, 10]
+    tf = synth.hidden_tf(5, n=11)
+    c = [cam(1, (2.0, 2.0, -6.0), (0, 0, 1), win=(-0.2, 0.2, -0.2, 0.2), w=3, h=2)]
+    g = np.random.default_rng(2).normal(size=(1, 2, 3, 4))
+    sc = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5, ert=2.0)
+    _, dvol, amb = oracle.backward(sc, c, g, "composite", ambiguity=True)
+    tf2 = tf.copy()
+    tf2[8] = 2 * tf[7] - tf[6]     # the left segment's slope continued past node 7
+    _, dvol2 = oracle.backward(oracle.Scene(vol, tf2, 0.0, 10.0, step=0.5, ert=2.0), c, g, "composite")
+    d = np.abs(dvol2 - dvol)
+    assert d.max() > 0 and np.all(d <= amb + 1e-12)
+    vol3 = np.full((12, 4, 4), 7.4, np.float32)  # between nodes 7 and 8
+    _, _, amb3 = oracle.backward(oracle.Scene(vol3, tf, 0.0, 10.0, step=0.5, ert=2.0), c, g, "composite",
+                                 ambiguity=True)
+    assert np.all(amb3 == 0)
+
+
+def test_adjoint_termination_alternative_bound():
+    """A ray whose termination is within rounding of the threshold may stop one sample
+    earlier: the bound must cover the gradient of that outcome (termination moved one
+    sample earlier by a threshold just below the earlier sample's accumulated alpha)."""
+    a = float(np.float32(0.1))
+    vol = np.broadcast_to(np.linspace(1.0, 2.0, 60, dtype=np.float32)[:, None, None], (60, 3, 3)).copy()
+    tf = np.array([[0.3, 0.6, 0.2, a], [0.9, 0.1, 0.5, a]], np.float32)
+    c = [cam(0, (1.5, 1.5, -1.3), (0, 0, 1))]
+    g = np.array([0.3, -0.2, 0.5, 0.7]).reshape(1, 1, 1, 4)
+    n = 44
+    ert = 1 - (1 - a) ** n - 1e-12
+    sc = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5, ert=ert)
+    assert oracle.render(sc, c[0], "composite")["flags"][0] & 4
+    _, dvol, amb = oracle.backward(sc, c, g, "composite", ambiguity=True)
+    _, dvol_early = oracle.backward(sc, c, g, "composite", ert=1 - (1 - a) ** (n - 1) - 1e-12)
+    d = np.abs(dvol_early - dvol)
+    assert d.max() > 0 and np.all(d <= amb + 1e-12)
+    # far from the threshold: no flag, and no ambiguity away from table nodes
+    sc2 = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5, ert=0.995)
+    assert not oracle.render(sc2, c[0], "composite")["flags"][0]
+    assert np.all(oracle.backward(sc2, c, g, "composite", ambiguity=True)[2] == 0)
