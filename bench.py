@@ -174,12 +174,44 @@ def load_touch_table():
 def oracle_sample(vol_rounded, tf, cam, pixels, cfg):
     """Time the FP64 oracle on the listed pixels, both modes; returns (samples, seconds, results)."""
     import oracle
-    sc = oracle.Scene(vol_rounded, tf, -1.0, 20.0, cfg["step"], cfg["ert"])
+    # the ambiguity windows of the composite follow the image-order marcher's error model
+    far = max(abs(x) for x in cam["eye"]) + max(abs(x) for x in cam["win"]) + max(vol_rounded.shape)
+    sc = oracle.Scene(vol_rounded, tf, -1.0, 20.0, cfg["step"], cfg["ert"],
+                      pos_err=oracle.pos_err_marcher(cfg["step"], far))
     t0 = time.perf_counter()
     rc = oracle.render(sc, cam, "composite", pixels)
     rm = oracle.render(sc, cam, "mip", pixels)
     dt = time.perf_counter() - t0
     return int(rc["nsamples"].sum() + rm["nsamples"].sum()), dt, (rc, rm)
+
+
+def summarise_extras(ex):
+    """The few figures of the extra measurements that the headline is read with."""
+    out = {}
+
+    def pick(name, keys):
+        d = ex.get(name) or {}
+        v = {k: (round(d[k], 4) if isinstance(d.get(k), float) else d.get(k)) for k in keys if k in d}
+        if "error" in d:
+            v["error"] = str(d["error"])[:120]
+        if v:
+            out[name] = v
+
+    pick("paths", ["composite_ray_ms", "composite_layered_ms", "composite_sortlast_ms", "mip_brick_ms",
+                   "mip_ray_ms"])
+    pick("wall", ["mip_batched_ms", "mip_25_single_ms", "mip_batching_speedup", "composite_batched_ms",
+                  "composite_batching_speedup", "mip_speedup_vs_fp32_single", "composite_speedup_vs_fp32_single"])
+    pick("diff", ["forward_ms", "backward_ms"])
+    h = (ex.get("hipass") or {}).get("8000x8000") or {}
+    if h:
+        out["hipass_8000"] = {k: round(h[k], 3) for k in ("mip_ms", "composite_ms", "pyramid_tile0_ms")
+                              if k in h}
+    o = ex.get("ooc") or {}
+    if o:
+        out["ooc"] = {k: (round(o[k], 4) if isinstance(o[k], float) else o[k]) for k in o
+                      if k in ("cold_frame_s", "warm_frame_s", "orbit", "h2d_floor_s", "generate_s",
+                               "mip_frame_s", "composite_frame_s")}
+    return out
 
 
 def sample_pixels(W, H, n, seed):
@@ -612,6 +644,7 @@ def run_ours(a):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
+        "storage_dtype": a.storage,
         "data": "synthetic",
         "config": workload_config(a.storage, world),
         "ms_per_frame": {"composite": None, "mip_brick_kernel": mip_ms},
@@ -694,6 +727,13 @@ def run_ours(a):
             res["extras"][name]["wall_s"] = time.time() - t0
             torch.cuda.empty_cache()
     if rank == 0:
+        # the detailed extras go on a line of their own (no "metric" key) before the
+        # result line, and the result line carries a short summary of them, so that the
+        # result line stays short enough to be kept whole
+        extras = res.pop("extras", None)
+        if extras is not None:
+            print(json.dumps({"extras": extras}), flush=True)
+            res["extras_summary"] = summarise_extras(extras)
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as tdist

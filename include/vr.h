@@ -274,7 +274,7 @@ vr_status vr_set_path(vr_ctx* ctx, vr_path path);
 vr_status vr_set_sample_counter(vr_ctx* ctx, unsigned long long* device_counter);
 
 /* Failure-detection self-test.  Runs, on `stream`, one thread that waits with
- * the brick pass's bounded mbarrier wait (shortened to 2^14 polls) on a barrier
+ * the brick pass's bounded mbarrier wait (its 2 s bound shortened to 1 ms) on a barrier
  * phase that no copy will complete, so that the wait gives up and records the
  * device status word exactly as an expired wait of a render would; then
  * synchronises the stream.  Returns VR_OK once the status word is set (the
@@ -294,10 +294,10 @@ vr_status vr_set_kernel_events(vr_ctx* ctx, void* start, void* stop);
 /*
  * Allocation-free MIP render.  The paper has no counterpart: this is a
  * service to callers of this library that cannot allocate device memory while
- * they render -- code that records work while a stream is being captured into
- * a CUDA graph (an allocation there fails the capture), code that must not
- * trigger the device-wide synchronisation cudaMalloc can imply, and programs
- * whose device memory is managed by another allocator.  vr_render's brick path
+ * they render -- real-time loops that must not meet the device-wide
+ * synchronisation cudaMalloc can imply, and programs whose device memory is
+ * owned by another allocator or held to a fixed budget, so that a library
+ * allocating behind their back would break it.  vr_render's brick path
  * allocates its per-pixel scratch on first use of a larger image; this call
  * instead takes its scratch (per-pixel sample ranges, per-pixel running
  * maxima, the work counter) from one fixed array compiled into the library,
@@ -311,8 +311,10 @@ vr_status vr_set_kernel_events(vr_ctx* ctx, void* start, void* stop);
  * (width * height), else VR_ERR_INVALID_ARG; bricks of at least 32 voxels,
  * else VR_ERR_UNSUPPORTED.
  * Set-up: the first call on each device looks up the device address of the
- * scratch array (with that device current); make that first call before any
- * stream capture.
+ * scratch array (with that device current) and keeps it for the life of the
+ * process; make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) after that first call is not supported: the kept address
+ * would then be stale.
  * Sharing: every call on a device uses the same scratch array, which keeps the
  * last call's contents; each call rewrites what it reads before reading it.
  * Calls whose GPU work overlaps (on different streams, or from several

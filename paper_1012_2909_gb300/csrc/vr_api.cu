@@ -665,7 +665,7 @@ vr_status vr_selftest_wait_timeout(vr_ctx* ctx, void* stream) {
     DevGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     VR_CK(cudaGetLastError(), "vr_selftest_wait_timeout: pending CUDA error");
-    VR_CK(launch_wait_probe(ctx->status_dev, 1LL << 14, s), "vr_selftest_wait_timeout: launch");
+    VR_CK(launch_wait_probe(ctx->status_dev, 1000000ull, s), "vr_selftest_wait_timeout: launch");  // 1 ms
     VR_CK(cudaStreamSynchronize(s), "vr_selftest_wait_timeout: wait");
     if (*ctx->status_host != (int)kDevWaitTimeout)
         return fail(ctx, VR_ERR_INTERNAL, "vr_selftest_wait_timeout: the bounded wait did not expire");

@@ -580,7 +580,11 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     if (cam < ncams) build_segments<T, ONE, GROUP>(P, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[0], tid);
     bool ok = mbar_wait(&bar, phase, P.status);
     phase ^= 1u;
-    if (!__syncthreads_and(ok)) return;  // no copy is in flight after a failed wait of the only load
+    // A failed wait (2 s without the copy completing) means a stalled copy: the CTA
+    // stops here and the next call reports the status.  That recovery assumes the
+    // copy never lands; one that completed later would write into the shared memory
+    // of a CTA that has exited.
+    if (!__syncthreads_and(ok)) return;
     for (;;) {
         const int nlong = s_cnt[chunk & 1][0], nshort = s_cnt[chunk & 1][1];
         if (tid == 0) {

@@ -177,6 +177,7 @@ struct Seg {
     int n;          // samples in this segment
     long long base; // element offset of the slot
     int brick;      // linear brick id
+    float ox, oy, oz;  // brick origin (voxels)
 };
 
 // Start a segment at sample k: pick the brick holding p_k (any brick whose
@@ -212,6 +213,9 @@ __device__ __forceinline__ bool seg_begin(const Ray& r, int k, const VolDev& v, 
     n = min(n, min(cap, r.k1 - k));
     s.n = n;
     s.brick = (bz * v.nby + by) * v.nbx + bx;
+    s.ox = (float)(bx << v.log2B);
+    s.oy = (float)(by << v.log2B);
+    s.oz = (float)(bz << v.log2B);
     const int slot = v.table[s.brick];
     s.base = (long long)slot * v.slot_elems;
     return slot >= 0;
@@ -275,18 +279,109 @@ __device__ __forceinline__ float fetch_trilinear_pair(const T* __restrict__ slot
     return fmaf(fz, b1 - b0, b0);
 }
 
+// Sub-anchor of a ray inside a segment: the sample k's slot coordinate g = G + q0
+// split into an integer corner G (as the element offset `base` of voxel G in the
+// slot) and a remainder q0 in [0, 1] rounded once from float-float.  The samples
+// k + j that follow sit at G + q0 + j e, so for j < kAnchorSpan the FP32
+// coordinate q = q0 + j e stays below 1 + kAnchorSpan |e| in magnitude: the
+// position keeps about 2^-24 of that magnitude, not of the brick edge.
+struct Anchor {
+    float qx, qy, qz;     // remainder at the anchor sample
+    float lox, loy, loz;  // clamp of q to the slot: [-G, B + 0.999 - G]
+    float hix, hiy, hiz;
+    int base;             // element offset of voxel G in the slot
+};
+
+constexpr int kAnchorSpan = 12;  // samples per sub-anchor
+
+__device__ __forceinline__ Anchor anchor_at(const Ray& r, int k, const VolDev& v, const Seg& s) {
+    const ff kk = ff_of_int(k);
+    const float org[3] = {s.ox, s.oy, s.oz};
+    float q[3], lo[3], hi[3];
+    int G[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const ff p = ff_add(r.o[a], ff_mul(r.e[a], kk));
+        // p.hi - origin + 1/2 is exact (multiples of ulp(p.hi), at most B + 2 apart)
+        const float gh = __fadd_rn(__fsub_rn(p.hi, org[a]), 0.5f);
+        const float g0 = floorf(gh);
+        q[a] = __fadd_rn(__fsub_rn(gh, g0), p.lo);
+        G[a] = (int)g0;
+        lo[a] = -g0;
+        hi[a] = __fadd_rn((float)v.B - g0, 0.999f);
+    }
+    Anchor A;
+    A.qx = q[0];
+    A.qy = q[1];
+    A.qz = q[2];
+    A.lox = lo[0];
+    A.loy = lo[1];
+    A.loz = lo[2];
+    A.hix = hi[0];
+    A.hiy = hi[1];
+    A.hiz = hi[2];
+    A.base = (G[2] * v.rows + G[1]) * v.pitch + G[0];
+    return A;
+}
+
+// fetch_trilinear at slot coordinate G + q for the anchor's G: the same lerps on the
+// same voxels, with the corner index split as base(G) + index(floor q).
+template <typename T>
+__device__ __forceinline__ float fetch_near(const T* __restrict__ slot, const VolDev& v, const Anchor& A,
+                                            float qx, float qy, float qz) {
+    qx = fminf(fmaxf(qx, A.lox), A.hix);
+    qy = fminf(fmaxf(qy, A.loy), A.hiy);
+    qz = fminf(fmaxf(qz, A.loz), A.hiz);
+    const float fx0 = floorf(qx), fy0 = floorf(qy), fz0 = floorf(qz);
+    const float fx = qx - fx0, fy = qy - fy0, fz = qz - fz0;
+    const int slab = v.rows * v.pitch;
+    const T* p = slot + A.base + ((int)fz0 * v.rows + (int)fy0) * v.pitch + (int)fx0;
+    const float c000 = ld_voxel(p), c100 = ld_voxel(p + 1);
+    const float c010 = ld_voxel(p + v.pitch), c110 = ld_voxel(p + v.pitch + 1);
+    const float c001 = ld_voxel(p + slab), c101 = ld_voxel(p + slab + 1);
+    const float c011 = ld_voxel(p + slab + v.pitch), c111 = ld_voxel(p + slab + v.pitch + 1);
+    const float a0 = fmaf(fx, c100 - c000, c000), a1 = fmaf(fx, c110 - c010, c010);
+    const float a2 = fmaf(fx, c101 - c001, c001), a3 = fmaf(fx, c111 - c011, c011);
+    const float b0 = fmaf(fy, a1 - a0, a0), b1 = fmaf(fy, a3 - a2, a2);
+    return fmaf(fz, b1 - b0, b0);
+}
+
+// fetch_trilinear_pair at slot coordinate G + q for the anchor's G (see fetch_near).
+template <typename T>
+__device__ __forceinline__ float fetch_near_pair(const T* __restrict__ slot, const T* __restrict__ slot1,
+                                                 const VolDev& v, const Anchor& A, float qx, float qy, float qz) {
+    qx = fminf(fmaxf(qx, A.lox), A.hix);
+    qy = fminf(fmaxf(qy, A.loy), A.hiy);
+    qz = fminf(fmaxf(qz, A.loz), A.hiz);
+    const float fx0 = floorf(qx), fy0 = floorf(qy), fz0 = floorf(qz);
+    const float fx = qx - fx0, fy = qy - fy0, fz = qz - fz0;
+    const int i = A.base + ((int)fz0 * v.rows + (int)fy0) * v.pitch + (int)fx0;
+    const int w = i >> 1;
+    const int hp = v.pitch >> 1, hs = (v.rows * v.pitch) >> 1;  // a row and a slab in words
+    const T* p = (i & 1) ? slot1 : slot;
+    const float2 c00 = ld_pair<T>(p, w), c10 = ld_pair<T>(p, w + hp);
+    const float2 c01 = ld_pair<T>(p, w + hs), c11 = ld_pair<T>(p, w + hs + hp);
+    const float a0 = fmaf(fx, c00.y - c00.x, c00.x), a1 = fmaf(fx, c10.y - c10.x, c10.x);
+    const float a2 = fmaf(fx, c01.y - c01.x, c01.x), a3 = fmaf(fx, c11.y - c11.x, c11.x);
+    const float b0 = fmaf(fy, a1 - a0, a0), b1 = fmaf(fy, a3 - a2, a2);
+    return fmaf(fz, b1 - b0, b0);
+}
+
 // True when every sample of brick b is certain to have opacity exactly 0: its
-// stored maximum (which bounds every trilinear sample in it) maps below the
-// transparent nodes 0..zero_top.  Values below the maximum, and NaN, map to
-// lower nodes, and a lookup between two zero-alpha nodes returns 0, so such a
-// segment leaves (C, T) unchanged and can be skipped.
+// stored maximum bounds every trilinear sample in it up to the FP32 rounding of
+// the lerps (a sample can exceed it by a few ulps, which can carry it past one
+// node boundary but not two), so the skip asks that the segment above the
+// maximum's segment be transparent too: the maximum's lower node plus 2 is at
+// most zero_top.  Values below the maximum, and NaN, map to lower nodes, and a
+// lookup between two zero-alpha nodes returns 0, so such a segment leaves
+// (C, T) unchanged and can be skipped.
 __device__ __forceinline__ int tf_node(int n, float vmin, float inv_range, float val, float& x);
 __device__ __forceinline__ bool brick_transparent(const VolDev& v, const TFDev& tf, int b) {
     if (!v.range_max || tf.zero_top < 1) return false;
     const unsigned int e = v.range_max[b];
     const float mx = __uint_as_float((e & 0x80000000u) ? (e & 0x7fffffffu) : ~e);
     float x;
-    return tf_node(tf.n, tf.vmin, tf.inv_range, mx, x) + 1 <= tf.zero_top;
+    return tf_node(tf.n, tf.vmin, tf.inv_range, mx, x) + 2 <= tf.zero_top;
 }
 
 // Table position x of a value and its lower node i (node-centred, clamped):

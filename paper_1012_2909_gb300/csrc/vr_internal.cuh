@@ -209,7 +209,7 @@ long long pyramid_levels(int w, int h, int tlog2, std::vector<int>& ws, std::vec
                          std::vector<long long>& offs);
 cudaError_t launch_pyramid(const float4* in, int w, int h, int tlog2, float4* out, cudaStream_t s);
 // Bounded-wait self-test (vr_selftest.cu): one waiter that gives up after `polls`.
-cudaError_t launch_wait_probe(int* status, long long polls, cudaStream_t s);
+cudaError_t launch_wait_probe(int* status, unsigned long long limit_ns, cudaStream_t s);
 int adjoint_threads();
 int adjoint_blocks_per_sm(vr_dtype dt, int mode, int ntf);
 cudaError_t launch_adjoint(const AdjParams& p, vr_dtype dt, int grid, cudaStream_t s);

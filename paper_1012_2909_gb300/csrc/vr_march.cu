@@ -2,22 +2,23 @@
 // tiles handed out by a persistent scheduler (one atomic counter per launch).
 //
 // Per ray (the discretisation of include/vr.h, vr_render): float-float ray
-// set-up and box interval; brick-by-brick traversal, each segment anchored in
-// float-float and stepped in FP32 brick-local coordinates; trilinear fetch from
-// the ghosted brick (x-neighbour pairs with one load each when the store's
-// shifted copy is kept); transfer-function lookup from shared memory;
-// front-to-back "over" with early termination, or maximum-intensity
-// projection.
+// set-up and box interval; brick-by-brick traversal; inside a brick the samples
+// are re-anchored in float-float every kAnchorSpan samples and stepped in FP32
+// relative to the anchor's voxel, so each position is within 13 u (u = 2^-24)
+// voxels of exact at the 0.5-voxel step; trilinear fetch from the ghosted brick
+// (x-neighbour pairs with one load each when the store's shifted copy is kept);
+// transfer-function lookup from shared memory; front-to-back "over" with early
+// termination, or maximum-intensity projection.
 #include "vr_device.cuh"
 
 namespace vr {
 
 namespace {
 
-constexpr int kSegCap = 128;  // samples between float-float re-anchors
+constexpr int kSegCap = 1 << 20;  // a brick segment is cut only where the ray leaves the brick
 // Samples fetched together per step.  The marcher waits on its gathers, so more
 // loads in flight beat more resident warps: with the register count left free
-// (launch bound 256 x 1), 4 measured fastest for single loads (3: +2 %, 6: +2 %,
+// (launch bound 256 x 2: at most 128 registers, two CTAs per SM), 4 measured fastest for single loads (3: +2 %, 6: +2 %,
 // 2: +9 %; capping registers at 64 for more warps cost 30 %), and 6 with the
 // paired loads, which need fewer registers per sample (4: +7 %, 3: +13 %,
 // 8: +15 %; survey composite over the orbit).
@@ -25,7 +26,7 @@ constexpr int kMarchUnroll = 4;
 constexpr int kMarchUnrollPaired = 6;
 
 template <typename T, int MODE, bool PAIRED>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 2)
 k_march(const __grid_constant__ MarchParams P) {
     constexpr int U = PAIRED ? kMarchUnrollPaired : kMarchUnroll;
     __shared__ float4 s_tf[kMaxTF];
@@ -54,7 +55,7 @@ k_march(const __grid_constant__ MarchParams P) {
                                                         // rejoins at the next shuffle
         Ray r;
         const bool hit = make_ray(P.cams[cam], px, py, P.vol, ff{P.step_hi, P.step_lo}, r);
-        float c0 = 0.f, c1 = 0.f, c2 = 0.f, Tr = 1.f, m = -INFINITY;
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, Tr = 1.f, m_ = -INFINITY;
         if (hit) {
             const float3 e32 = make_float3(r.e[0].hi, r.e[1].hi, r.e[2].hi);
             int k = r.k0;
@@ -68,37 +69,44 @@ k_march(const __grid_constant__ MarchParams P) {
                 }
                 const T* slot = pool + s.base;
                 const T* slot1 = PAIRED ? pool1 + s.base : nullptr;
-                // U samples fetched together (more loads in flight), then
-                // composited in order; a fetch past the segment repeats its last sample
-                for (int j = 0; j < s.n && !done; j += U) {
-                    float v[U];
+                int j = 0;  // samples of this segment done
+                while (j < s.n && !done) {
+                    // sub-anchor at sample k + j; U samples fetched together (more loads
+                    // in flight), then composited in order; a fetch past the span
+                    // repeats its last sample
+                    const Anchor A = anchor_at(r, k + j, P.vol, s);
+                    const int m = min(kAnchorSpan, s.n - j);
+                    for (int i = 0; i < m && !done; i += U) {
+                        float v[U];
 #pragma unroll
-                    for (int q = 0; q < U; ++q) {
-                        const float fj = (float)min(j + q, s.n - 1);
-                        const float gx = fmaf(fj, e32.x, s.gx), gy = fmaf(fj, e32.y, s.gy),
-                                    gz = fmaf(fj, e32.z, s.gz);
-                        v[q] = PAIRED ? fetch_trilinear_pair<T>(slot, slot1, P.vol, gx, gy, gz)
-                                      : fetch_trilinear<T>(slot, P.vol, gx, gy, gz);
-                    }
+                        for (int q = 0; q < U; ++q) {
+                            const float fi = (float)min(i + q, m - 1);
+                            const float qx = fmaf(fi, e32.x, A.qx), qy = fmaf(fi, e32.y, A.qy),
+                                        qz = fmaf(fi, e32.z, A.qz);
+                            v[q] = PAIRED ? fetch_near_pair<T>(slot, slot1, P.vol, A, qx, qy, qz)
+                                          : fetch_near<T>(slot, P.vol, A, qx, qy, qz);
+                        }
 #pragma unroll
-                    for (int q = 0; q < U; ++q) {
-                        if (j + q >= s.n) break;
-                        if (MODE == VR_MIP) {
-                            m = fmaxf(m, v[q]);
-                        } else {
-                            const float4 c = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, v[q]);
-                            const float w = Tr * c.w;
-                            c0 = fmaf(w, c.x, c0);
-                            c1 = fmaf(w, c.y, c1);
-                            c2 = fmaf(w, c.z, c2);
-                            Tr = Tr * (1.f - c.w);
-                            if (1.f - Tr >= ert) {
-                                my_samples += (unsigned long long)(j + q + 1);
-                                done = true;
-                                break;
+                        for (int q = 0; q < U; ++q) {
+                            if (i + q >= m) break;
+                            if (MODE == VR_MIP) {
+                                m_ = fmaxf(m_, v[q]);
+                            } else {
+                                const float4 c = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, v[q]);
+                                const float w = Tr * c.w;
+                                c0 = fmaf(w, c.x, c0);
+                                c1 = fmaf(w, c.y, c1);
+                                c2 = fmaf(w, c.z, c2);
+                                Tr = Tr * (1.f - c.w);
+                                if (1.f - Tr >= ert) {
+                                    my_samples += (unsigned long long)(j + i + q + 1);
+                                    done = true;
+                                    break;
+                                }
                             }
                         }
                     }
+                    j += m;
                 }
                 if (!done) my_samples += (unsigned long long)s.n;
                 k += s.n;
@@ -107,9 +115,9 @@ k_march(const __grid_constant__ MarchParams P) {
         const long long pix = ((long long)cam * P.height + py) * P.width + px;
         if (MODE == VR_MIP) {
             float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (m > -INFINITY) o = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, m);
+            if (m_ > -INFINITY) o = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, m_);
             P.out_rgba[pix] = o;
-            if (P.out_max) P.out_max[pix] = m;
+            if (P.out_max) P.out_max[pix] = m_;
         } else {
             P.out_rgba[pix] = make_float4(c0, c1, c2, 1.f - Tr);
         }

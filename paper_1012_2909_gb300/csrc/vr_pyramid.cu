@@ -38,7 +38,7 @@ __device__ __forceinline__ long long pix_index(int x, int y, int w, int tlog2) {
     if (tlog2 < 0) return (long long)y * w + x;
     const int m = (1 << tlog2) - 1;
     const int tx = (w + m) >> tlog2;
-    return ((long long)((y >> tlog2) * tx + (x >> tlog2)) << (2 * tlog2)) + ((y & m) << tlog2) + (x & m);
+    return (((long long)(y >> tlog2) * tx + (x >> tlog2)) << (2 * tlog2)) + ((y & m) << tlog2) + (x & m);
 }
 
 __global__ void __launch_bounds__(kPyrThreads) k_pyramid(const __grid_constant__ PyrParams P) {

@@ -1,11 +1,10 @@
 // Allocation-free MIP entry point (vr_render_mip_noalloc).
 //
 // vr_render's brick path allocates its per-pixel scratch with cudaMalloc the
-// first time it meets a larger image.  Some callers cannot allow that: code
-// that records work while a stream is being captured into a CUDA graph (an
-// allocation there is an error), code that must not hit the device-wide
-// synchronisation that cudaMalloc may imply, and applications whose device
-// memory is owned by another allocator.  This entry point renders the same
+// first time it meets a larger image.  Some callers cannot allow that:
+// real-time loops that must not hit the device-wide synchronisation that
+// cudaMalloc may imply, and applications whose device memory is owned by
+// another allocator or held to a fixed budget.  This entry point renders the same
 // MIP with its scratch -- per-pixel sample ranges, per-pixel running maxima
 // and the work counter -- taken from one fixed array compiled into the
 // library, and calls no allocating routine.
@@ -30,7 +29,8 @@ std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
 
 // Device address of the scratch area on `device`, which must be current.
-// Looked up once per device; later calls reuse the cached pointer.
+// Looked up once per device; later calls reuse the cached pointer, so a device
+// reset after the first call is not supported (the pointer would be stale).
 cudaError_t scratch_address(int device, void** out) {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);

@@ -10,10 +10,14 @@ namespace vr {
 
 enum DeviceStatus : int {
     kDevOk = 0,
-    kDevWaitTimeout = 1,   // an mbarrier wait exceeded its iteration bound
+    kDevWaitTimeout = 1,   // an mbarrier wait exceeded its time bound
 };
 
-constexpr long long kWaitSpinLimit = 1LL << 26;  // try_wait polls before giving up
+// A wait gives up after this much time on the GPU's global nanosecond timer.  A
+// copy of one staged cell takes microseconds, so a wait that runs out means a
+// copy that has stalled, not one that is merely slow under contention.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr long long kWaitIterCap = 1LL << 26;                // rounds of 32 polls, at most
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -50,12 +54,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false (and *status set) after
-// `limit` unsuccessful polls.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of `bar`; false (and *status set) once
+// `limit_ns` nanoseconds have passed without the phase completing.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status,
-                                          long long limit = kWaitSpinLimit) {
-    for (long long i = 0; i < limit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
+                                          unsigned long long limit_ns = kWaitLimitNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    // the time bound decides; the iteration cap only backs it up
+    for (long long it = 0; it < kWaitIterCap; ++it) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) break;
+    }
     if (status) atomicExch(status, (int)kDevWaitTimeout);
     return false;
 }

@@ -5,14 +5,39 @@ oracle's primary result, or -- for a ray the oracle flags as ambiguous (a first
 or last sample, or the termination sample, within rounding of its threshold) --
 against one of the oracle's alternative outcomes for that ray.
 """
+import copy
+
 import numpy as np
 
 import oracle
 
 
-def compare(gpu_rgba, scene, cam, mode, pixels=None, tol=1e-4, gpu_max=None, max_tol=None):
-    """gpu_rgba: (npix, 4) for the listed pixels (flat py*W+px; None = all).
-    Returns dict(max_err, n_flagged, n_variant, max_err_max)."""
+def far_extent(scene, cam):
+    """Largest coordinate magnitude (voxels) a sample of this view can have: the eye (or
+    the orthographic image plane) and the cube."""
+    return (max(abs(float(x)) for x in cam["eye"]) + max(abs(float(x)) for x in cam["win"]) +
+            max(scene.nx, scene.ny, scene.nz))
+
+
+def model_scene(scene, cam, mode, path):
+    """The scene with the error model of the render path under test (the oracle's
+    ambiguity windows follow from it): the image-order marcher ("auto" and "ray"
+    composite) re-anchors every 12 samples; the other paths step in brick-local FP32
+    (bound for 128^3 bricks, the largest edge used)."""
+    sc = copy.copy(scene)
+    far = far_extent(scene, cam)
+    if mode == "composite" and path in ("auto", "ray"):
+        sc.pos_err = oracle.pos_err_marcher(scene.step, far)
+    else:
+        sc.pos_err = oracle.pos_err_bricked(128, far)
+    return sc
+
+
+def compare(gpu_rgba, scene, cam, mode, pixels=None, tol=1e-4, gpu_max=None, max_tol=None,
+            path="auto"):
+    """gpu_rgba: (npix, 4) for the listed pixels (flat py*W+px; None = all), rendered by
+    render path `path`.  Returns dict(max_err, n_flagged, n_variant, max_err_max)."""
+    scene = model_scene(scene, cam, mode, path)
     ref = oracle.render(scene, cam, mode, pixels)
     g = np.asarray(gpu_rgba, dtype=np.float64).reshape(-1, 4)
     err = np.abs(g - ref["rgba"]).max(axis=1)
@@ -23,10 +48,10 @@ def compare(gpu_rgba, scene, cam, mode, pixels=None, tol=1e-4, gpu_max=None, max
         fl = int(ref["flags"][i])
         best = err[i]
         if fl:
-            for de, dk0, dk1 in oracle.variants(fl):
-                if (de, dk0, dk1) == (0.0, 0, 0):
+            for ds, dk0, dk1 in oracle.variants(fl):
+                if (ds, dk0, dk1) == (0, 0, 0):
                     continue
-                alt = oracle.render(scene, cam, mode, pix_all[i:i + 1], ert=scene.ert + de,
+                alt = oracle.render(scene, cam, mode, pix_all[i:i + 1], dstop=ds,
                                     dk0=dk0, dk1=dk1)
                 best = min(best, float(np.abs(g[i] - alt["rgba"][0]).max()))
         if best > tol:

@@ -41,7 +41,7 @@ def test_hipass_static_render_sampled_pixels():
             img = out.reshape(-1, 4)[torch.from_numpy(pix).cuda()].cpu().numpy()
             mxs = mx.reshape(-1)[torch.from_numpy(pix).cuda()].cpu().numpy()
             st = compare(img, sc, cam, mode, pixels=pix, tol=1e-4,
-                         gpu_max=mxs if mode == "mip" else None, max_tol=2e-3)
+                         gpu_max=mxs if mode == "mip" else None, max_tol=2e-3, path=path)
             print(W, H, mode, path, st)
             assert st["nsamples"] > (1_000_000 if mode == "mip" else 50_000), st  # the view sees the cube
             del out, mx

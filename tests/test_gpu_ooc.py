@@ -58,7 +58,7 @@ def test_streamed_equals_oracle_and_in_core(cube, storage):
         assert torch.equal(out, ref)
         for i, c in enumerate(cams):
             compare(out[i].cpu().numpy().reshape(-1, 4), sc, c, mode, tol=1e-4,
-                    gpu_max=mx[i].cpu().numpy() if mode == "mip" else None, max_tol=2e-3)
+                    gpu_max=mx[i].cpu().numpy() if mode == "mip" else None, max_tol=2e-3, path=path)
     st = vr.vr_get_stream_stats(rs.ctx)
     print(st)
     assert st["bricks_fetched"] > 9 and st["batches"] > 1 and st["bytes_h2d"] > 0

@@ -106,7 +106,7 @@ def test_odd_step_sizes(vr, step):
         img, mx = _render(vr, vol, tf, cams, mode, brick=32, step=step, path=path)
         for i, c in enumerate(cams):
             st = compare(img[i].reshape(-1, 4), sc, c, mode, tol=1e-4,
-                         gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
+                         gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3, path=path)
             assert st["nsamples"] > 0
 
 
@@ -126,7 +126,7 @@ def test_transfer_function_and_termination_extremes(vr, ntf, ert, vrange):
                           path=path)
         for i, c in enumerate(cams):
             compare(img[i].reshape(-1, 4), sc, c, mode, tol=1e-4,
-                    gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
+                    gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3, path=path)
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
@@ -168,7 +168,7 @@ def test_fine_step(vr):
         img, mx = _render(vr, vol, tf, cams, mode, brick=8 if path == "ray" else 32, step=0.05, path=path)
         for i, c in enumerate(cams):
             st = compare(img[i].reshape(-1, 4), sc, c, mode, tol=1e-4,
-                         gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
+                         gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3, path=path)
             assert st["nsamples"] > 0
 
 
@@ -185,7 +185,7 @@ def test_distant_narrow_view(vr):
     for mode, path in (("composite", "ray"), ("mip", "ray"), ("mip", "brick")):
         img, mx = _render(vr, vol, tf, [cam], mode, brick=32, path=path)
         st = compare(img[0].reshape(-1, 4), sc, cam, mode, tol=1e-4,
-                     gpu_max=mx[0] if mode == "mip" else None, max_tol=2e-3)
+                     gpu_max=mx[0] if mode == "mip" else None, max_tol=2e-3, path=path)
         assert st["nsamples"] > 0
 
 
@@ -401,7 +401,7 @@ def test_survey_workload_sampled_pixels(vr, storage):
         mxs = mx.cpu().numpy().reshape(2, -1)
         for i, c in enumerate(cams):
             st = compare(img[i][pix], sc, c, mode, pixels=pix, tol=1e-4,
-                         gpu_max=mxs[i][pix] if mode == "mip" else None, max_tol=2e-3)
+                         gpu_max=mxs[i][pix] if mode == "mip" else None, max_tol=2e-3, path=path)
             print(storage, mode, path, i, st)
     r.close()
 
@@ -446,7 +446,7 @@ def test_sortlast_and_layered_composite(vr, storage):
         sc_on = oracle.Scene(rounded, tf, -1.0, 20.0, 0.5, 0.99)
         img, _ = _render(vr, vol, tf, cams, "composite", storage=storage, brick=brick, path="sortlast")
         for i, c in enumerate(cams):
-            compare(img[i].reshape(-1, 4), sc_off, c, "composite", tol=1e-4)
+            compare(img[i].reshape(-1, 4), sc_off, c, "composite", tol=1e-4, path="sortlast")
         img, _ = _render(vr, vol, tf, cams, "composite", storage=storage, brick=brick, path="layered")
         for i, c in enumerate(cams):
-            compare(img[i].reshape(-1, 4), sc_on, c, "composite", tol=1e-4)
+            compare(img[i].reshape(-1, 4), sc_on, c, "composite", tol=1e-4, path="layered")

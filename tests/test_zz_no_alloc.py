@@ -1,5 +1,6 @@
 """vr_render_mip_noalloc: the MIP render for callers that cannot allocate device memory
-while they render (for example while a stream is being captured into a CUDA graph).
+while they render (real-time loops that must not meet cudaMalloc's implicit
+synchronisation, programs whose device memory belongs to another allocator).
 It must give the same images as vr_render's brick path, call after call, although every
 call reuses one fixed scratch array inside the library.
 
