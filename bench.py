@@ -209,8 +209,9 @@ def summarise_extras(ex):
     o = ex.get("ooc") or {}
     if o:
         out["ooc"] = {k: (round(o[k], 4) if isinstance(o[k], float) else o[k]) for k in o
-                      if k in ("cold_frame_s", "warm_frame_s", "orbit", "h2d_floor_s", "generate_s",
-                               "mip_frame_s", "composite_frame_s")}
+                      if k in ("cold_frame_s", "warm_frame_s", "composite_orbit_s", "composite_orbit_generate_s",
+                               "composite_orbit_floor_s", "mip_frame_s", "mip_bricks", "h2d_link_gbs",
+                               "generate_gbs")}
     return out
 
 
@@ -433,10 +434,21 @@ def extra_diff(dev):
             "forward_ms": fwd, "step_ms": both, "backward_ms": both - fwd}
 
 
-def extra_ooc(dev, cache_gib=32):
-    """Out-of-core: 4096 x 4096 x 8192 FP16 cube (256 GiB) produced brick by brick from
-    the generator, 32 GiB HBM cache; one composite frame of the orbit (front bricks
-    only: rays terminate early, bricks behind them are never fetched)."""
+def extra_ooc(dev, cache_gib=32, frames=10):
+    """Out-of-core: 4096 x 4096 x 8192 FP16 cube (256 GiB) produced brick by brick from the
+    generator into page-locked memory and streamed to a 32 GiB HBM cache.
+
+    * composite: the 10-frame orbit (10 deg steps) at 1920 x 1080; a frame fetches only
+      the bricks in front of terminated rays that are not cached yet;
+    * MIP: every brick a ray crosses is needed (about 275 GB a frame at full view), so the
+      MIP frames cover a bounded share of the cube, labelled: the central panel of a
+      10 x 10 split of the same 1920 x 1080 view (1/100 of the image, all depths), at
+      1920 x 1080, for the first 3 orbit positions.
+
+    Per frame the stages are reported apart: host generation (time inside the region
+    callback), the host-to-device link (the bytes copied and their floor at the measured
+    pinned copy rate), the host's waits on the device, and the rest; the frame's floor is
+    its largest stage."""
     import torch
 
     import paper_1012_2909_gb300 as vr
@@ -444,35 +456,56 @@ def extra_ooc(dev, cache_gib=32):
     cfg = synth.CONFIGS["ooc"]
     p = cfg["cube"]
     dims = (p["nx"], p["ny"], p["nz"])
-    r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
-    fn, user = synth.region_callback(p)
-    vr.vr_load_cube_streamed(r.ctx, fn, user, dims, "f16", cache_bytes=cache_gib << 30)
-    r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
-    r.set_camera(synth.orbit_view(dims, 0.0))
-    t0 = time.time()
-    r.render("composite")
-    torch.cuda.synchronize()
-    cold = time.time() - t0
-    st0 = vr.vr_get_stream_stats(r.ctx)
-    t0 = time.time()
-    r.render("composite")  # warm: the front bricks are cached
-    torch.cuda.synchronize()
-    warm = time.time() - t0
-    st = vr.vr_get_stream_stats(r.ctx)
-    r.close()
     # the host-to-device link: one pinned 1 GiB buffer copied a few times
     host = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
     devb = torch.empty(1 << 28, dtype=torch.float32, device=f"cuda:{dev}")
     h2d_ms = _events_ms(lambda: devb.copy_(host, non_blocking=True), 4)
     h2d_gbs = host.numel() * 4 / (h2d_ms / 1e3) / 1e9
     del host, devb
-    return {"workload": "4096x4096x8192 FP16 (256 GiB) streamed from the generator, 32 GiB cache, "
-                        "1920x1080, composite frame 0",
-            "cold_frame_s": cold, "warm_frame_s": warm, "bricks_fetched": st0["bricks_fetched"],
-            "bricks_culled": st0["bricks_culled"], "h2d_gb": st0["bytes_h2d"] / 1e9,
-            "generate_s": st0["generate_s"], "warm_refetched": st["bricks_fetched"] - st0["bricks_fetched"],
-            "h2d_link_gbs": h2d_gbs, "h2d_floor_s": st0["bytes_h2d"] / 1e9 / h2d_gbs,
-            "generate_gbs": st0["bytes_h2d"] / 1e9 / max(st0["generate_s"], 1e-9)}
+    torch.cuda.empty_cache()
+    r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
+    fn, user = synth.region_callback(p)
+    vr.vr_load_cube_streamed(r.ctx, fn, user, dims, "f16", cache_bytes=cache_gib << 30)
+    r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
+    W, H = cfg["image"]
+
+    def frame(cam, mode):
+        r.set_camera(cam)
+        st0 = vr.vr_get_stream_stats(r.ctx)
+        t0 = time.time()
+        r.render(mode)
+        torch.cuda.synchronize()
+        wall = time.time() - t0
+        st = vr.vr_get_stream_stats(r.ctx)
+        d = {k: st[k] - st0[k] for k in ("bricks_fetched", "bricks_culled", "bytes_h2d", "batches",
+                                         "generate_s", "wait_s")}
+        link = d["bytes_h2d"] / 1e9 / h2d_gbs
+        stages = {"generate_s": d["generate_s"], "link_floor_s": link, "device_wait_s": d["wait_s"],
+                  "other_s": max(0.0, wall - d["generate_s"] - d["wait_s"])}
+        return {"wall_s": wall, "bricks_fetched": d["bricks_fetched"], "bricks_culled": d["bricks_culled"],
+                "batches": d["batches"], "h2d_gb": d["bytes_h2d"] / 1e9, **stages,
+                "floor_s": max(stages["generate_s"], link), "wall_over_floor": wall / max(1e-9, max(
+                    stages["generate_s"], link))}
+
+    cams = synth.orbit(dims, frames, 10.0, W, H)
+    comp = [frame(c, "composite") for c in cams]
+    warm = frame(cams[-1], "composite")  # the last view again: everything cached
+    mip = []
+    for c in cams[:3]:
+        big = dict(c, width=W * 10, height=H * 10)
+        mip.append(frame(synth.wall_views(big, 10, 10)[55], "mip"))
+    r.close()
+    tot = lambda xs, k: sum(x[k] for x in xs)  # noqa: E731
+    return {"workload": "4096x4096x8192 FP16 (256 GiB) streamed from the generator, 32 GiB cache, 1920x1080; "
+                        f"composite: {frames}-frame orbit (10 deg steps); MIP: central 1/100 panel of the "
+                        "view (bounded share of the cube), 3 orbit positions",
+            "h2d_link_gbs": h2d_gbs,
+            "composite_frames": comp, "composite_warm_repeat": warm, "mip_frames": mip,
+            "composite_orbit_s": tot(comp, "wall_s"), "composite_orbit_generate_s": tot(comp, "generate_s"),
+            "composite_orbit_floor_s": tot(comp, "floor_s"),
+            "mip_frame_s": [m["wall_s"] for m in mip], "mip_bricks": [m["bricks_fetched"] for m in mip],
+            "cold_frame_s": comp[0]["wall_s"], "warm_frame_s": warm["wall_s"],
+            "generate_gbs": tot(comp, "h2d_gb") / max(tot(comp, "generate_s"), 1e-9)}
 
 
 # ------------------------------------------------------------------------------ our arm

@@ -406,6 +406,55 @@ vr_status vr_image_pyramid(vr_ctx* ctx, const float* rgba, int32_t width, int32_
 vr_status vr_overlay_boxes(vr_ctx* ctx, const vr_camera* cams, int32_t ncams, const double* boxes, int64_t nbox,
                            const float* colours, float* rgba, void* stream);
 
+/*
+ * Object-space sort-last across ranks (Abstract and Sec. 1: a cube larger than one
+ * node's memory is split into parts that are rendered separately, and the parts'
+ * images are combined).  A rank renders the partial images of the bricks it holds
+ * (vr_sortlast_partials); the partials are exchanged so that the owner of a band
+ * of image rows holds every partial that covers it, whoever rendered it; the owner
+ * folds them in visibility order (vr_sortlast_fold).  The exchange itself is the
+ * caller's (the Python package's dist module moves them with torch.distributed);
+ * these calls only produce and consume partial images.  Both act on camera 0 and
+ * require exactly one camera, an in-core cube and a transfer function
+ * (VR_ERR_STATE otherwise).
+ *
+ * A partial image covers the brick's footprint (the conservative pixel rectangle of
+ * its box), float4 per pixel, row-major over the rectangle:
+ *   VR_COMPOSITE: (C0, C1, C2, T): the brick's samples of the pixel's ray
+ *     composited front to back from T = 1, no termination (premultiplied colour,
+ *     transmittance);
+ *   VR_MIP: (m, 0, 0, 0): the largest sample value, -inf without samples.
+ */
+typedef struct {
+    int32_t brick;          /* linear brick id, (bz * nby + by) * nbx + bx              */
+    int32_t key;            /* visibility key: ascending is front to back (reading R9)  */
+    int32_t x0, y0, x1, y1; /* pixel rectangle, inclusive; empty when x1 < x0          */
+    int64_t offset;         /* float4 index of the rectangle's first pixel in the buffer */
+} vr_footprint;
+
+/* Footprints and partial images of the listed bricks (host array of n distinct
+ * linear ids; n = 0, a rank that holds no brick, renders nothing).  foot (host, n entries) receives the footprint of bricks[i]
+ * at index i, offsets packed from 0 in list order; *needed the float4 count of
+ * all of them.  partial (device, 16-byte aligned, capacity float4) receives the
+ * images; NULL only sizes the call (foot and *needed are still filled).
+ * Errors: VR_ERR_INVALID_ARG for a bad or repeated id, a NULL foot or needed, or
+ * a capacity below *needed; VR_ERR_STATE as above. */
+vr_status vr_sortlast_partials(vr_ctx* ctx, vr_mode mode, const int32_t* bricks, int32_t n,
+                               vr_footprint* foot, float* partial, int64_t capacity, int64_t* needed,
+                               void* stream);
+
+/* Fold n partial images (device buffer partial of capacity float4; host
+ * footprints foot, distinct brick ids, any order) over the image rows [y0, y1) of
+ * camera 0: per pixel, the partials covering it in ascending (key, brick):
+ * VR_COMPOSITE: C += T C_b, T *= T_b from (0, 1), out = (C, 1 - T) premultiplied;
+ * VR_MIP: m = max of the maxima, out = TF(m) straight, (0,0,0,0) for -inf.
+ * out_rgba (device, 16-byte aligned): width * (y1 - y0) float4, row-major.
+ * n = 0 folds nothing (transparent band).  Errors: VR_ERR_INVALID_ARG for bad
+ * rows, a footprint outside the image or beyond capacity, repeated ids. */
+vr_status vr_sortlast_fold(vr_ctx* ctx, vr_mode mode, const float* partial, int64_t capacity,
+                           const vr_footprint* foot, int32_t n, int32_t y0, int32_t y1, float* out_rgba,
+                           void* stream);
+
 /* Layout of the loaded cube; VR_ERR_STATE if none is loaded. */
 vr_status vr_get_cube_info(const vr_ctx* ctx, vr_cube_info* info);
 

@@ -92,6 +92,9 @@ def _load():
             lib.orc_backward.argtypes = [_P, _P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int]
             lib.orc_touch.restype = ctypes.c_int
             lib.orc_touch.argtypes = [_P, _P, _P, ctypes.c_int64, _P, ctypes.c_int]
+            lib.orc_brick_partial.restype = ctypes.c_int
+            lib.orc_brick_partial.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int64, _P,
+                                              ctypes.c_int64, _P, _P, _P, _P]
             lib.orc_round_bf16.restype = None
             lib.orc_round_bf16.argtypes = [_P, _P, ctypes.c_int64]
             lib.orc_overlay.restype = ctypes.c_int
@@ -216,6 +219,28 @@ def render_sortlast(scene: Scene, cam: dict, brick: int, mode: str = "composite"
     if rc:
         raise ValueError("orc_render_sortlast: bad arguments")
     return dict(rgba=rgba, max=vmax)
+
+
+def brick_partial(scene: Scene, cam: dict, brick: int, brick_id: int, pixels=None) -> dict:
+    """Partial image of one brick of the brick^3 decomposition: per pixel (flat py*W+px;
+    None = whole image) the brick's samples composited front to back from T = 1 with no
+    termination, as ct = (C0, C1, C2, T), plus their maximum and count, and the brick's
+    visibility key (ascending = front to back)."""
+    lib = _load()
+    s = scene._struct(0, 2.0)
+    c = camera_struct(cam)
+    if pixels is None:
+        pixels = np.arange(cam["width"] * cam["height"], dtype=np.int64)
+    pix = np.ascontiguousarray(pixels, dtype=np.int64)
+    ct = np.zeros((pix.size, 4), np.float64)
+    mx = np.zeros(pix.size, np.float64)
+    ns = np.zeros(pix.size, np.int64)
+    key = ctypes.c_int64(0)
+    rc = lib.orc_brick_partial(ctypes.byref(s), ctypes.byref(c), int(brick), int(brick_id), _ptr(pix),
+                               pix.size, _ptr(ct), _ptr(mx), _ptr(ns), ctypes.byref(key))
+    if rc:
+        raise ValueError("orc_brick_partial: bad arguments")
+    return dict(ct=ct, max=mx, nsamples=ns, key=int(key.value))
 
 
 def backward(scene: Scene, cams: list, dimg: np.ndarray, mode: str = "composite", *,

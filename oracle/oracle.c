@@ -580,6 +580,81 @@ int orc_render_sortlast(const orc_scene* s, const orc_camera* cam, int64_t brick
     return 0;
 }
 
+/* ------------------------------------------------- per-brick partial images */
+/*
+ * The partial image of one brick (the paper's parts of a cube rendered apart
+ * and combined, Abstract and Sec. 1): for each listed pixel, the ray's samples
+ * owned by brick `brick` of the B^3 decomposition (the brick containing the
+ * sample position, floor(p/B) clamped to the brick grid, as in the sort-last
+ * form above) composited front to back from T = 1 with no termination, as
+ * (C, T) -- premultiplied colour and transmittance -- plus their maximum (MIP)
+ * and count.  Folding the bricks' partials per pixel in ascending visibility
+ * key (ties by brick id) with C += T C_b, T *= T_b gives orc_render_sortlast.
+ * out_ct: npix x 4 (C0, C1, C2, T); out_max, out_ns: npix each (may be NULL);
+ * out_key receives the brick's visibility key.  Returns 0, or -1 on bad arguments.
+ */
+int orc_brick_partial(const orc_scene* s, const orc_camera* cam, int64_t B, int64_t brick,
+                      const int64_t* pix, int64_t npix, double* out_ct, double* out_max,
+                      int64_t* out_ns, int64_t* out_key)
+{
+    if (!scene_ok(s) || !cam || !pix || !out_ct || !out_key || B <= 0) return -1;
+    int64_t nb[3] = {(s->nx + B - 1) / B, (s->ny + B - 1) / B, (s->nz + B - 1) / B};
+    if (brick < 0 || brick >= nb[0] * nb[1] * nb[2]) return -1;
+    int64_t bb[3] = {brick % nb[0], (brick / nb[0]) % nb[1], brick / (nb[0] * nb[1])};
+    int64_t key = 0;
+    for (int64_t i = 0; i < npix; ++i) {
+        int64_t px = pix[i] % cam->width, py = pix[i] / cam->width;
+        double o[3], d[3];
+        int64_t k0, k1;
+        int flags = 0;
+        camera_ray(cam, px, py, o, d);
+        double C[3] = {0, 0, 0}, T = 1.0, m = -INFINITY;
+        int64_t n = 0;
+        if (ray_samples(s, o, d, &k0, &k1, &flags)) {
+            for (int64_t k = k0; k < k1; ++k) {
+                double t = (double)k * s->step;
+                double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+                int inside = 1;
+                for (int a = 0; a < 3; ++a) {
+                    int64_t b = (int64_t)floor(p[a] / (double)B);
+                    if (b < 0) b = 0;
+                    if (b > nb[a] - 1) b = nb[a] - 1;
+                    if (b != bb[a]) inside = 0;
+                }
+                if (!inside) continue;
+                double v = trilinear(s, p, NULL, NULL, NULL);
+                ++n;
+                if (v > m) m = v;
+                tf_eval_t e;
+                tf_lookup(s, v, &e);
+                double a = e.rgba[3];
+                for (int c = 0; c < 3; ++c) C[c] += T * a * e.rgba[c];
+                T *= (1.0 - a);
+            }
+        }
+        for (int c = 0; c < 3; ++c) out_ct[4 * i + c] = C[c];
+        out_ct[4 * i + 3] = T;
+        if (out_max) out_max[i] = m;
+        if (out_ns) out_ns[i] = n;
+    }
+    /* visibility key of the brick, as in trace_sortlast */
+    int64_t e[3];
+    for (int a = 0; a < 3; ++a) e[a] = (int64_t)floor(cam->eye[a] / (double)B);
+    double c0[3];
+    if (cam->type == 0) {
+        double o[3];
+        camera_ray(cam, 0, 0, o, c0);
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (cam->type == 1)
+            key += bb[a] > e[a] ? bb[a] - e[a] : e[a] - bb[a];
+        else
+            key += c0[a] > 0 ? bb[a] : (c0[a] < 0 ? -bb[a] : 0);
+    }
+    *out_key = key;
+    return 0;
+}
+
 /* ------------------------------------------------------------- step 7: adjoint */
 typedef struct {
     int64_t k;        /* sample index */

@@ -108,8 +108,16 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     "vr_image_pyramid": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "vr_overlay_boxes": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P]),
+    "vr_sortlast_partials": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int32, _P, _P, ctypes.c_int64,
+                                            ctypes.POINTER(ctypes.c_int64), _P]),
+    "vr_sortlast_fold": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int64, _P, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "vr_last_error": (ctypes.c_char_p, [_P]),
 }
+
+# vr_footprint (include/vr.h) as a numpy record
+FOOTPRINT = np.dtype([("brick", "<i4"), ("key", "<i4"), ("x0", "<i4"), ("y0", "<i4"), ("x1", "<i4"),
+                      ("y1", "<i4"), ("offset", "<i8")])
 
 _lock = threading.Lock()
 _lib = None
@@ -240,6 +248,35 @@ def vr_render_mip_noalloc(ctx, out_rgba, out_max=None, stream=None, device: int 
                                    None if out_max is None else ctypes.c_void_p(out_max.data_ptr()),
                                    _stream_handle(stream, device))
     _check(ctx, st, "vr_render_mip_noalloc")
+
+
+def vr_sortlast_partials(ctx, mode: str, bricks, partial=None, stream=None, device: int = 0):
+    """Footprints (numpy FOOTPRINT array, in the order of `bricks`) and the float4 count of
+    the partial images of the listed bricks for camera 0; with `partial` (a float32 device
+    tensor of at least 4 x that many values) also renders the images into it."""
+    ids = np.ascontiguousarray(bricks, dtype=np.int32)
+    foot = np.zeros(ids.size, FOOTPRINT)
+    need = ctypes.c_int64(0)
+    cap = 0 if partial is None else partial.numel() // 4
+    st = load_library().vr_sortlast_partials(
+        ctx, MODES[mode], ids.ctypes.data_as(ctypes.c_void_p) if ids.size else None, int(ids.size),
+        foot.ctypes.data_as(ctypes.c_void_p) if ids.size else None,
+        None if partial is None else ctypes.c_void_p(partial.data_ptr()), cap, ctypes.byref(need),
+        _stream_handle(stream, device))
+    _check(ctx, st, "vr_sortlast_partials")
+    return foot, need.value
+
+
+def vr_sortlast_fold(ctx, mode: str, partial, foot, y0: int, y1: int, out, stream=None, device: int = 0):
+    """Fold the partial images (float32 device tensor, footprints `foot`, FOOTPRINT array)
+    over rows [y0, y1) of camera 0 into out (device tensor, (y1 - y0) x width x 4)."""
+    f = np.ascontiguousarray(foot, dtype=FOOTPRINT)
+    cap = 0 if partial is None else partial.numel() // 4
+    st = load_library().vr_sortlast_fold(
+        ctx, MODES[mode], None if partial is None or cap == 0 else ctypes.c_void_p(partial.data_ptr()), cap,
+        f.ctypes.data_as(ctypes.c_void_p), int(f.size), int(y0), int(y1), ctypes.c_void_p(out.data_ptr()),
+        _stream_handle(stream, device))
+    _check(ctx, st, "vr_sortlast_fold")
 
 
 def vr_pyramid_layout(width: int, height: int, tile: int = 0):

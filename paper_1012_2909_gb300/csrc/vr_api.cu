@@ -101,6 +101,10 @@ struct vr_ctx {
     size_t tf_partials_n = 0;
     int* status_host = nullptr;    // mapped, page-locked device status word
     int* status_dev = nullptr;
+    // distributed sort-last (vr_sortlast_partials / vr_sortlast_fold)
+    int* dist_ids = nullptr;       // brick subset | tile prefix | fold order | count
+    long long dist_cap = 0;        // bricks the buffer holds
+    BrickFoot* dist_foot = nullptr;
     unsigned long long* sample_counter = nullptr;  // caller-owned
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;  // caller-owned profiling events
 };
@@ -383,7 +387,8 @@ vr_status vr_destroy(vr_ctx* ctx) {
         if (ctx->enc) cudaFree(ctx->enc);
         if (ctx->tf_partials) cudaFree(ctx->tf_partials);
         for (void* p : {(void*)ctx->foot, (void*)ctx->order, (void*)ctx->tile_start, (void*)ctx->layer_buf,
-                        (void*)ctx->partial_used, (void*)ctx->partial, (void*)ctx->state})
+                        (void*)ctx->partial_used, (void*)ctx->partial, (void*)ctx->state,
+                        (void*)ctx->dist_ids, (void*)ctx->dist_foot})
             if (p) cudaFree(p);
         if (ctx->host_rb) cudaFreeHost(ctx->host_rb);
         if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
@@ -1734,6 +1739,202 @@ vr_status vr_overlay_boxes(vr_ctx* ctx, const vr_camera* cams, int32_t ncams, co
     VR_CK(launch_overlay(reinterpret_cast<const OverlayCam*>(base), ncams, reinterpret_cast<const double*>(base + cam_b),
                          nbox, reinterpret_cast<const float*>(base + cam_b + box_b), ctx->ov_key, rgba, W, H, s),
           "vr_overlay_boxes: launch");
+    return VR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Checks shared by the two distributed sort-last calls.
+vr_status dist_checks(vr_ctx* ctx, vr_mode mode, const char* what) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (mode != VR_COMPOSITE && mode != VR_MIP) return fail(ctx, VR_ERR_INVALID_ARG, std::string(what) + ": bad mode");
+    if (!ctx->has_cube || ctx->ooc) return fail(ctx, VR_ERR_STATE, std::string(what) + ": no in-core cube loaded");
+    if (!ctx->has_tf) return fail(ctx, VR_ERR_STATE, std::string(what) + ": no transfer function set");
+    if (ctx->cams.size() != 1) return fail(ctx, VR_ERR_STATE, std::string(what) + ": exactly one camera is required");
+    return VR_OK;
+}
+
+vr_status dist_scratch(vr_ctx* ctx, long long nbricks) {
+    if (nbricks * 3 + 2 <= ctx->dist_cap * 3 + 2 && ctx->dist_ids) return VR_OK;
+    if (ctx->dist_ids) cudaFree(ctx->dist_ids);
+    if (ctx->dist_foot) cudaFree(ctx->dist_foot);
+    ctx->dist_ids = nullptr;
+    ctx->dist_foot = nullptr;
+    ctx->dist_cap = 0;
+    VR_CK(cudaMalloc(&ctx->dist_ids, sizeof(int) * (size_t)(3 * nbricks + 2)), "sort-last exchange: scratch");
+    VR_CK(cudaMalloc(&ctx->dist_foot, sizeof(BrickFoot) * (size_t)nbricks), "sort-last exchange: scratch");
+    ctx->dist_cap = nbricks;
+    return VR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vr_status vr_sortlast_partials(vr_ctx* ctx, vr_mode mode, const int32_t* bricks, int32_t n, vr_footprint* foot,
+                               float* partial, int64_t capacity, int64_t* needed, void* stream) {
+    vr_status st = dist_checks(ctx, mode, "vr_sortlast_partials");
+    if (st != VR_OK) return st;
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long nbricks = (long long)ctx->nbx * ctx->nby * ctx->nbz;
+    if (!needed || n < 0 || n > nbricks || (n > 0 && (!bricks || !foot)))
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_partials: bad brick list, foot or needed");
+    *needed = 0;
+    if (n == 0) return VR_OK;  // a rank that holds no brick renders nothing
+    if (reinterpret_cast<uintptr_t>(partial) % 16)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_partials: partial must be 16-byte aligned");
+    std::vector<char> seen((size_t)nbricks, 0);
+    for (int i = 0; i < n; ++i) {
+        if (bricks[i] < 0 || bricks[i] >= nbricks || seen[(size_t)bricks[i]])
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_partials: brick id out of range or repeated");
+        seen[(size_t)bricks[i]] = 1;
+    }
+    const CamDev& cd = ctx->cams[0];
+    const int W = cd.width, H = cd.height;
+    const long long img = (long long)W * H;
+    st = ensure_pixel_scratch(ctx, img);
+    if (st != VR_OK) return st;
+    st = dist_scratch(ctx, nbricks);
+    if (st != VR_OK) return st;
+    // footprints and keys of every brick (the producer of render_ooc's batches)
+    SortParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.vol = vol_dev(ctx);
+    sp.tf = tf_dev(ctx);
+    split(ctx->opt.step, sp.step, sp.step_lo);
+    sp.ert = 2.0f;
+    sp.mode = mode;
+    sp.krange = ctx->krange;
+    PixelParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.vol = sp.vol;
+    pp.tf = sp.tf;
+    split(ctx->opt.step, pp.step_hi, pp.step_lo);
+    pp.width = W;
+    pp.height = H;
+    pp.krange = ctx->krange;
+    pp.enc = ctx->enc;
+    pp.cam = ray_cam(cd);
+    VR_CK(launch_pixel_setup(pp, s), "vr_sortlast_partials: pixel set-up");
+    std::vector<int> order, layer_start;
+    std::vector<BrickFoot> all;
+    st = ooc_footprints(ctx, cd, sp, order, layer_start, all, s);
+    if (st != VR_OK) return st;
+    if (layer_start.empty() || layer_start.back() == 0)  // no brick visible: nothing was read back
+        all.assign((size_t)nbricks, BrickFoot{make_int4(0, 0, -1, -1), 0, 0, 0});
+    // packed offsets in list order; the visible listed bricks and their tile prefix
+    std::vector<int> sub, tiles(1, 0);
+    long long off = 0;
+    for (int i = 0; i < n; ++i) {
+        BrickFoot& f = all[(size_t)bricks[i]];
+        const bool vis = f.rect.z >= f.rect.x && f.rect.w >= f.rect.y;
+        vr_footprint& o = foot[i];
+        o.brick = bricks[i];
+        o.key = f.key;
+        o.x0 = vis ? f.rect.x : 0;
+        o.y0 = vis ? f.rect.y : 0;
+        o.x1 = vis ? f.rect.z : -1;
+        o.y1 = vis ? f.rect.w : -1;
+        o.offset = off;
+        f.offset = off;
+        if (vis) {
+            off += (long long)(f.rect.z - f.rect.x + 1) * (f.rect.w - f.rect.y + 1);
+            sub.push_back(bricks[i]);
+            tiles.push_back(tiles.back() + ((f.rect.z - f.rect.x + 1 + 7) / 8) * ((f.rect.w - f.rect.y + 1 + 3) / 4));
+        } else {
+            f.rect = make_int4(0, 0, -1, -1);
+        }
+    }
+    *needed = off;
+    if (!partial) return VR_OK;
+    if (capacity < off) return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_partials: capacity below the images' size");
+    if (sub.empty()) return VR_OK;
+    int* d_sub = ctx->dist_ids;
+    int* d_tile = ctx->dist_ids + nbricks;
+    VR_CK(cudaMemcpyAsync(sp.foot, all.data(), sizeof(BrickFoot) * (size_t)nbricks, cudaMemcpyHostToDevice, s),
+          "vr_sortlast_partials: upload");
+    VR_CK(cudaMemcpyAsync(d_sub, sub.data(), sizeof(int) * sub.size(), cudaMemcpyHostToDevice, s),
+          "vr_sortlast_partials: upload");
+    VR_CK(cudaMemcpyAsync(d_tile, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, s),
+          "vr_sortlast_partials: upload");
+    sp.sub_order = d_sub;
+    sp.sub_tile = d_tile;
+    sp.sub_n = (int)sub.size();
+    sp.partial = reinterpret_cast<float4*>(partial);
+    sp.work = ctx->work;
+    VR_CK(cudaMemsetAsync(sp.work, 0, sizeof(int), s), "vr_sortlast_partials: scheduler reset");
+    VR_CK(launch_brick_partial(sp, ctx->dtype, false, 0, 0, ctx->num_sms * 8, s), "vr_sortlast_partials: partials");
+    // the host vectors are read by the copies above before the call returns
+    VR_CK(cudaStreamSynchronize(s), "vr_sortlast_partials: upload");
+    return VR_OK;
+}
+
+vr_status vr_sortlast_fold(vr_ctx* ctx, vr_mode mode, const float* partial, int64_t capacity,
+                           const vr_footprint* foot, int32_t n, int32_t y0, int32_t y1, float* out_rgba,
+                           void* stream) {
+    vr_status st = dist_checks(ctx, mode, "vr_sortlast_fold");
+    if (st != VR_OK) return st;
+    DevGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const CamDev& cd = ctx->cams[0];
+    const int W = cd.width, H = cd.height;
+    const long long nbricks = (long long)ctx->nbx * ctx->nby * ctx->nbz;
+    if (!out_rgba || reinterpret_cast<uintptr_t>(out_rgba) % 16 || reinterpret_cast<uintptr_t>(partial) % 16)
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_fold: out_rgba must be given, 16-byte aligned");
+    if (y0 < 0 || y1 > H || y0 >= y1) return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_fold: bad rows");
+    if (n < 0 || n > nbricks || (n > 0 && (!foot || !partial)))
+        return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_fold: bad footprint list");
+    st = dist_scratch(ctx, nbricks);
+    if (st != VR_OK) return st;
+    std::vector<BrickFoot> all((size_t)nbricks, BrickFoot{make_int4(0, 0, -1, -1), 0, 0, 0});
+    std::vector<char> seen((size_t)nbricks, 0);
+    std::vector<int> order;
+    for (int i = 0; i < n; ++i) {
+        const vr_footprint& f = foot[i];
+        if (f.brick < 0 || f.brick >= nbricks || seen[(size_t)f.brick])
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_fold: brick id out of range or repeated");
+        seen[(size_t)f.brick] = 1;
+        if (f.x1 < f.x0 || f.y1 < f.y0) continue;  // empty: covers no pixel
+        if (f.x0 < 0 || f.y0 < 0 || f.x1 >= W || f.y1 >= H || f.offset < 0 ||
+            f.offset + (long long)(f.x1 - f.x0 + 1) * (f.y1 - f.y0 + 1) > capacity)
+            return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_fold: footprint outside the image or the buffer");
+        BrickFoot& b = all[(size_t)f.brick];
+        b.rect = make_int4(f.x0, f.y0, f.x1, f.y1);
+        b.key = f.key;
+        b.offset = f.offset;
+        order.push_back(f.brick);
+    }
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return all[(size_t)a].key != all[(size_t)b].key ? all[(size_t)a].key < all[(size_t)b].key : a < b;
+    });
+    int* d_order = ctx->dist_ids + 2 * nbricks;
+    int* d_count = ctx->dist_ids + 3 * nbricks + 1;
+    const int cnt = (int)order.size();
+    VR_CK(cudaMemcpyAsync(ctx->dist_foot, all.data(), sizeof(BrickFoot) * (size_t)nbricks, cudaMemcpyHostToDevice, s),
+          "vr_sortlast_fold: upload");
+    if (cnt > 0)
+        VR_CK(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * (size_t)cnt, cudaMemcpyHostToDevice, s),
+              "vr_sortlast_fold: upload");
+    VR_CK(cudaMemcpyAsync(d_count, &cnt, sizeof(int), cudaMemcpyHostToDevice, s), "vr_sortlast_fold: upload");
+    SortParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.vol = vol_dev(ctx);
+    sp.tf = tf_dev(ctx);
+    if (!cam_ff(cd, sp.cam)) return fail(ctx, VR_ERR_INVALID_ARG, "vr_sortlast_fold: camera basis is singular");
+    sp.mode = mode;
+    sp.foot = ctx->dist_foot;
+    sp.order = d_order;
+    sp.max_layers = 0;
+    sp.layer_start = d_count;  // layer_start[max_layers] = the number of ordered partials
+    sp.partial = const_cast<float4*>(reinterpret_cast<const float4*>(partial));
+    sp.out_rgba = reinterpret_cast<float4*>(out_rgba);
+    sp.fold_y0 = y0;
+    sp.fold_rows = y1 - y0;
+    VR_CK(launch_sortlast_fold(sp, s), "vr_sortlast_fold: fold");
+    VR_CK(cudaStreamSynchronize(s), "vr_sortlast_fold: upload");  // host vectors read by the copies
     return VR_OK;
 }
 

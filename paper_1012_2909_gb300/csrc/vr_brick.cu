@@ -387,10 +387,9 @@ __global__ void k_cell_list(const __grid_constant__ BrickParams P, CellDesc* __r
 constexpr int kShortRounds = 3;
 
 template <typename T, bool ONE, int G>
-__device__ __forceinline__ void build_segments(const BrickParams& P, int cam_, int4 rect, float3 lo,
-                                               int c0, SegRec* segs, int* cnt, int tid) {
-    const int cam = ONE ? 0 : cam_;  // one camera: constant-offset parameter reads
-    const CamFF& c = P.cams[cam];
+__device__ __forceinline__ void build_segments(const BrickParams& P, const CamFF& c, int cam_, int4 rect,
+                                               float3 lo, int c0, SegRec* segs, int* cnt, int tid) {
+    const int cam = ONE ? 0 : cam_;
     const long long img = (long long)P.width * P.height;
     const int2* kr_img = P.krange + (long long)cam * img;
     const float4* pd_img = P.pixdir ? P.pixdir + 2 * (long long)cam * img : nullptr;
@@ -512,9 +511,21 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     __shared__ int s_u[3];
     __shared__ int s_cnt[2][2];  // per chunk parity: long, short records
     __shared__ int s_claim[2];
+    // the camera of the chunk being built: one camera reads its parameters at
+    // constant offsets; with several, the chunk's camera is copied here so that
+    // the segment build does not index the parameter space dynamically
+    __shared__ __align__(16) CamFF s_cam;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nvalid = *count;
+    auto stage_cam = [&](int cam) {
+        if (ONE) return;
+        const int* src = reinterpret_cast<const int*>(&P.cams[cam]);
+        int* dst = reinterpret_cast<int*>(&s_cam);
+        for (int i = tid; i < (int)(sizeof(CamFF) / sizeof(int)); i += kBrickThreads) dst[i] = src[i];
+        __syncthreads();
+    };
+    const CamFF& cam_ref = ONE ? P.cams[0] : s_cam;
     const int ncams = ONE ? 1 : P.ncams;
     // warp 0: claim the next unit into descriptor slot `slot`, with its pixel
     // rectangle for every camera (camera 0 from the list, the others one lane each)
@@ -577,7 +588,10 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     uint32_t phase = 0;
     next_chunk(cur, cam, c0);
     float3 lo = make_float3(s_desc[cur].lo.x, s_desc[cur].lo.y, s_desc[cur].lo.z);
-    if (cam < ncams) build_segments<T, ONE, GROUP>(P, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[0], tid);
+    if (cam < ncams) {
+        stage_cam(cam);
+        build_segments<T, ONE, GROUP>(P, cam_ref, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[0], tid);
+    }
     bool ok = mbar_wait(&bar, phase, P.status);
     phase ^= 1u;
     // A failed wait (2 s without the copy completing) means a stalled copy: the CTA
@@ -598,7 +612,8 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
         c0 += kSegCap;
         next_chunk(cur, cam, c0);
         if (cam < ncams) {  // more pixels of the same cell
-            build_segments<T, ONE, GROUP>(P, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[chunk & 1], tid);
+            stage_cam(cam);
+            build_segments<T, ONE, GROUP>(P, cam_ref, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[chunk & 1], tid);
             __syncthreads();
             continue;
         }
@@ -610,7 +625,10 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
         c0 = 0;
         next_chunk(cur, cam, c0);
         lo = make_float3(s_desc[cur].lo.x, s_desc[cur].lo.y, s_desc[cur].lo.z);
-        if (cam < ncams) build_segments<T, ONE, GROUP>(P, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[chunk & 1], tid);
+        if (cam < ncams) {
+            stage_cam(cam);
+            build_segments<T, ONE, GROUP>(P, cam_ref, cam, s_rect[cur][cam], lo, c0, segs, s_cnt[chunk & 1], tid);
+        }
         // the slot after `cur` was last read two units ago: refill it now
         if (warp == 0) claim(cur == 2 ? 0 : cur + 1);
         ok = mbar_wait(&bar, phase, P.status);

@@ -148,7 +148,9 @@ struct SortParams {
     int* work;                        // zeroed work counter of a launch
     const int* sub_order;             // optional explicit brick subset (out-of-core batches)
     const int* sub_tile;              // its tile prefix (sub_n + 1)
-    int sub_n, pad3;
+    int sub_n, mode;                  // mode: VR_COMPOSITE partials (C, T) or VR_MIP maxima
+    int fold_y0, fold_rows;           // fold only rows [fold_y0, fold_y0 + fold_rows) into a
+                                      // band image (fold_rows = 0: the whole image)
 };
 
 // Per-pixel set-up and finalisation around the brick pass.

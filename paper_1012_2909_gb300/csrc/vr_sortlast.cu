@@ -11,6 +11,9 @@
 //     stored as (C, T) -- the brick's partial image;
 //   * k_sortlast_fold: per pixel, the partial images folded front to back in
 //     visibility order (C += T C_b, T *= T_b);
+//   * with P.mode == VR_MIP the partial image of a brick is the maximum of its
+//     samples per pixel (-inf without samples) and the fold takes the maximum,
+//     then the transfer function;
 //   * k_brick_partial<CARRIED>: the same march continuing each pixel's running
 //     (C, T) with per-sample early termination, one visibility layer of bricks
 //     per launch (no two bricks of a layer own samples of the same ray), and
@@ -291,6 +294,20 @@ k_brick_partial(const __grid_constant__ SortParams P, int layer_begin, int layer
         int ka, kb;
         const int2 kr = P.krange[pix];
         const bool any = kr.x < kr.y && brick_segment(P, px, py, kr, bx, by, bz, g, e, ka, kb);
+        if (!CARRIED && P.mode == VR_MIP) {  // the brick's maximum (object-space MIP)
+            float m = -INFINITY;
+            if (any) {
+                const T* slot = pool + (long long)P.vol.table[b] * P.vol.slot_elems;
+                for (int j = 0; j < kb - ka; ++j) {
+                    const float fj = (float)j;
+                    m = fmaxf(m, fetch_trilinear<T>(slot, P.vol, fmaf(fj, e[0], g[0]), fmaf(fj, e[1], g[1]),
+                                                    fmaf(fj, e[2], g[2])));
+                }
+            }
+            const int rw = rect.z - rect.x + 1;
+            P.partial[f.offset + (long long)(py - rect.y) * rw + (px - rect.x)] = make_float4(m, 0.f, 0.f, 0.f);
+            continue;
+        }
         if (any) {
             const T* slot = pool + (long long)P.vol.table[b] * P.vol.slot_elems;
             // at most ~4 B samples per brick: FP32 stepping from the float-float anchor
@@ -324,10 +341,11 @@ __global__ void __launch_bounds__(256) k_sortlast_fold(const __grid_constant__ S
     __shared__ int s_n, s_chunk_n;
     __shared__ int s_warp_cnt[8];
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * 16, y0 = blockIdx.y * 16;
+    const int ylim = P.fold_rows > 0 ? P.fold_y0 + P.fold_rows : P.cam.height;  // rows folded: [.., ylim)
+    const int x0 = blockIdx.x * 16, y0 = P.fold_y0 + blockIdx.y * 16;
     const int px = x0 + (tid & 15), py = y0 + (tid >> 4);
     const int nvis = P.layer_start[P.max_layers];
-    float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.f;
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.f, M = -INFINITY;
     for (int base = 0; base < nvis; base += 2048) {
         if (tid == 0) s_n = 0;
         __syncthreads();
@@ -359,22 +377,32 @@ __global__ void __launch_bounds__(256) k_sortlast_fold(const __grid_constant__ S
             __syncthreads();
         }
         const int n = s_n;
-        if (px < P.cam.width && py < P.cam.height) {
+        if (px < P.cam.width && py < ylim) {
             for (int q = 0; q < n; ++q) {
                 const BrickFoot f = P.foot[s_list[q]];
                 if (px < f.rect.x || px > f.rect.z || py < f.rect.y || py > f.rect.w) continue;
                 const int rw = f.rect.z - f.rect.x + 1;
                 const float4 p = P.partial[f.offset + (long long)(py - f.rect.y) * rw + (px - f.rect.x)];
-                C0 = fmaf(Tr, p.x, C0);
-                C1 = fmaf(Tr, p.y, C1);
-                C2 = fmaf(Tr, p.z, C2);
-                Tr *= p.w;
+                if (P.mode == VR_MIP) {
+                    M = fmaxf(M, p.x);
+                } else {
+                    C0 = fmaf(Tr, p.x, C0);
+                    C1 = fmaf(Tr, p.y, C1);
+                    C2 = fmaf(Tr, p.z, C2);
+                    Tr *= p.w;
+                }
             }
         }
         __syncthreads();
     }
-    if (px < P.cam.width && py < P.cam.height)
-        P.out_rgba[(long long)py * P.cam.width + px] = make_float4(C0, C1, C2, 1.f - Tr);
+    if (px < P.cam.width && py < ylim) {
+        const long long o = (long long)(py - P.fold_y0) * P.cam.width + px;
+        if (P.mode == VR_MIP)
+            P.out_rgba[o] = M > -INFINITY ? tf_lookup(P.tf.tab, P.tf.n, P.tf.vmin, P.tf.inv_range, M)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        else
+            P.out_rgba[o] = make_float4(C0, C1, C2, 1.f - Tr);
+    }
 }
 
 __global__ void k_state_init(const __grid_constant__ SortParams P) {
@@ -423,7 +451,8 @@ cudaError_t launch_brick_partial(const SortParams& p, vr_dtype dt, bool carried,
 }
 
 cudaError_t launch_sortlast_fold(const SortParams& p, cudaStream_t s) {
-    dim3 grid((p.cam.width + 15) / 16, (p.cam.height + 15) / 16);
+    const int rows = p.fold_rows > 0 ? p.fold_rows : p.cam.height;
+    dim3 grid((p.cam.width + 15) / 16, (rows + 15) / 16);
     k_sortlast_fold<<<grid, 256, 0, s>>>(p);
     return cudaGetLastError();
 }

@@ -59,6 +59,7 @@ def test_abi_struct_layouts():
     assert ctypes.sizeof(vr.vr_camera) == 8 + 12 * 8 + 4 * 8 + 8
     assert ctypes.sizeof(vr.vr_options) == 24
     assert ctypes.sizeof(vr.vr_cube_info) == 3 * 8 + 6 * 4 + 2 * 8
+    assert vr.FOOTPRINT.itemsize == 6 * 4 + 8  # vr_footprint
 
 
 def test_pyramid_layout_matches_the_oracle():

@@ -582,3 +582,29 @@ def test_adjoint_termination_alternative_bound():
     sc2 = oracle.Scene(vol, tf, 0.0, 10.0, step=0.5, ert=0.995)
     assert not oracle.render(sc2, c[0], "composite")["flags"][0]
     assert np.all(oracle.backward(sc2, c, g, "composite", ambiguity=True)[2] == 0)
+
+
+# -------------------------------------------------- per-brick partial images (sort-last)
+@pytest.mark.parametrize("brick", [8, 16])
+def test_brick_partials_fold_to_the_direct_render(brick):
+    """The bricks' partial images folded per pixel in ascending (key, brick id) with
+    C += T C_b, T *= T_b equal the direct render without termination (associativity of
+    "over"), their maxima give the MIP maximum, and their sample counts add up."""
+    sc = _small_scene()
+    dims = (sc.nx, sc.ny, sc.nz)
+    nb = [-(-d // brick) for d in dims]
+    for v in (synth.orbit_view(dims, 40.0, 20, 16), synth.ortho_view(dims, 20, 16)):
+        direct = oracle.render(sc, v, "composite", ert=2.0)
+        mip = oracle.render(sc, v, "mip")
+        parts = [oracle.brick_partial(sc, v, brick, b) for b in range(nb[0] * nb[1] * nb[2])]
+        order = sorted(range(len(parts)), key=lambda b: (parts[b]["key"], b))
+        C = np.zeros((direct["rgba"].shape[0], 3))
+        T = np.ones(direct["rgba"].shape[0])
+        for b in order:
+            C += T[:, None] * parts[b]["ct"][:, :3]
+            T *= parts[b]["ct"][:, 3]
+        np.testing.assert_allclose(C, direct["rgba"][:, :3], atol=1e-12)
+        np.testing.assert_allclose(1 - T, direct["rgba"][:, 3], atol=1e-12)
+        m = np.max([p_["max"] for p_ in parts], axis=0)
+        assert np.array_equal(m, mip["max"])
+        assert np.array_equal(np.sum([p_["nsamples"] for p_ in parts], axis=0), direct["nsamples"])
