@@ -628,7 +628,7 @@ int orc_brick_partial(const orc_scene* s, const orc_camera* cam, int64_t B, int6
                 tf_eval_t e;
                 tf_lookup(s, v, &e);
                 double a = e.rgba[3];
-                for (int c = 0; c < 3; ++c) C[c] += T * a * e.rgba[c];
+                for (int ch = 0; ch < 3; ++ch) C[ch] += T * a * e.rgba[ch];
                 T *= (1.0 - a);
             }
         }
