@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--storage", default="f16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--profile", choices=["mip", "composite", "both", "pyramid"], default=None,
+    ap.add_argument("--profile", choices=["mip", "composite", "both", "pyramid", "sortlast", "layered", "adjoint"],
+                    default=None,
                     help="only render --warmup + --steps orbit frames (for ncu); no timing legs")
     ap.add_argument("--cube", default=None,
                     help="NX,NY,NZ: override the cube size (same source density) for small captures")
@@ -442,8 +443,8 @@ def extra_ooc(dev, cache_gib=32, frames=10):
       the bricks in front of terminated rays that are not cached yet;
     * MIP: every brick a ray crosses is needed (about 275 GB a frame at full view), so the
       MIP frames cover a bounded share of the cube, labelled: the central panel of a
-      10 x 10 split of the same 1920 x 1080 view (1/100 of the image, all depths), at
-      1920 x 1080, for the first 3 orbit positions.
+      20 x 20 split of the same view (1/400 of the image, all depths), at 1920 x 1080, for
+      the first 2 orbit positions.
 
     Per frame the stages are reported apart: host generation (time inside the region
     callback), the host-to-device link (the bytes copied and their floor at the measured
@@ -491,14 +492,14 @@ def extra_ooc(dev, cache_gib=32, frames=10):
     comp = [frame(c, "composite") for c in cams]
     warm = frame(cams[-1], "composite")  # the last view again: everything cached
     mip = []
-    for c in cams[:3]:
-        big = dict(c, width=W * 10, height=H * 10)
-        mip.append(frame(synth.wall_views(big, 10, 10)[55], "mip"))
+    for c in cams[:2]:
+        big = dict(c, width=W * 20, height=H * 20)
+        mip.append(frame(synth.wall_views(big, 20, 20)[210], "mip"))  # panel (10, 10) of 20 x 20
     r.close()
     tot = lambda xs, k: sum(x[k] for x in xs)  # noqa: E731
     return {"workload": "4096x4096x8192 FP16 (256 GiB) streamed from the generator, 32 GiB cache, 1920x1080; "
-                        f"composite: {frames}-frame orbit (10 deg steps); MIP: central 1/100 panel of the "
-                        "view (bounded share of the cube), 3 orbit positions",
+                        f"composite: {frames}-frame orbit (10 deg steps); MIP: central 1/400 panel of the "
+                        "view (bounded share of the cube), 2 orbit positions",
             "h2d_link_gbs": h2d_gbs,
             "composite_frames": comp, "composite_warm_repeat": warm, "mip_frames": mip,
             "composite_orbit_s": tot(comp, "wall_s"), "composite_orbit_generate_s": tot(comp, "generate_s"),
@@ -853,6 +854,37 @@ def run_profile(a):
         r.close()
         return
 
+    if a.profile == "adjoint":
+        # forward + adjoint of the gradient workload (256^3 FP32, L2 loss against a hidden
+        # table's images), 8 of its 64 views at 512 x 512 per step
+        dcfg = synth.CONFIGS["diff"]
+        pd = dcfg["cube"]
+        ddims = (pd["nx"], pd["ny"], pd["nz"])
+        vol = synth.generate(pd)
+        views = synth.random_views(ddims, 8, seed=dcfg["view_seed"], width=512, height=512)
+        r = vr.Renderer(0, brick=128, step=dcfg["step"], ert=dcfg["ert"])
+        r.load_cube(vol, "f32")
+        r.set_camera(views)
+        r.set_transfer_function(synth.hidden_tf(dcfg["tf_seed"]), -1.0, 20.0)
+        target = r.render("composite").clone()
+        r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
+        dtf = torch.empty((256, 4), device="cuda")
+        dvol = torch.empty(vol.shape, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(a.warmup + a.steps):
+            if i == a.warmup:
+                torch.cuda.synchronize()
+                e0.record()
+            img = r.render("composite")
+            dimg = (2.0 * (img - target) / img.numel()).contiguous()
+            vr.vr_render_backward(r.ctx, "composite", dimg, dtf, dvol)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "adjoint", "cube": ddims, "views": len(views),
+                          "ms_per_step": e0.elapsed_time(e1) / max(a.steps, 1)}))
+        r.close()
+        return
+
     cfg = synth.CONFIGS[WORKLOAD]
     p = dict(cfg["cube"])
     if a.cube:
@@ -867,6 +899,9 @@ def run_profile(a):
     r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
     cams = synth.orbit(dims, cfg["frames"])
     modes = ["composite", "mip"] if a.profile == "both" else [a.profile]
+    if a.profile in ("sortlast", "layered"):  # the object-order composite paths
+        r.set_path(a.profile)
+        modes = ["composite"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n = a.warmup + a.steps
     for i in range(n):
