@@ -156,8 +156,10 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adjoint(const __grid_constant__ AdjParams P) {
     constexpr unsigned int FULL = 0xffffffffu;
-    extern __shared__ float s_grad[];  // (warps per block) x 4 channels x ntf
-    __shared__ float4 s_tf[kMaxTF];
+    // dynamic: (warps per block) x 4 channels x ntf table-gradient floats, then the
+    // ntf table entries (sized by the table, not kMaxTF, so more CTAs fit an SM)
+    extern __shared__ __align__(16) float s_grad[];
+    float4* s_tf = reinterpret_cast<float4*>(s_grad + kAdjWarps * 4 * P.tf.n);
     __shared__ RaySetup s_ray[kAdjWarps][32];
     __shared__ float s_ckT[kAdjWarps][kAdjMaxChunks];
     const int ntf = P.tf.n;
@@ -402,7 +404,7 @@ void* adj_pick(vr_dtype dt, int mode) {
 int adjoint_threads() { return kAdjThreads; }
 
 int adjoint_blocks_per_sm(vr_dtype dt, int mode, int ntf) {
-    const size_t smem = (size_t)(kAdjThreads / 32) * ntf * 4 * sizeof(float);
+    const size_t smem = (size_t)(kAdjThreads / 32) * ntf * 4 * sizeof(float) + (size_t)ntf * sizeof(float4);
     void* f = adj_pick(dt, mode);
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     int n = 0;
@@ -411,7 +413,7 @@ int adjoint_blocks_per_sm(vr_dtype dt, int mode, int ntf) {
 }
 
 cudaError_t launch_adjoint(const AdjParams& p, vr_dtype dt, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)(kAdjThreads / 32) * p.tf.n * 4 * sizeof(float);
+    const size_t smem = (size_t)(kAdjThreads / 32) * p.tf.n * 4 * sizeof(float) + (size_t)p.tf.n * sizeof(float4);
     void* f = adj_pick(dt, p.mode);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

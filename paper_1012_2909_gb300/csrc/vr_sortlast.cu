@@ -244,7 +244,13 @@ __global__ void k_tile_scan(const __grid_constant__ SortParams P) {
 
 // One warp per (brick, 8 x 4 tile of its rectangle); one thread per pixel.
 // Bricks of the ordered positions [start of layer l0, start of layer l1).
-template <typename T, bool CARRIED>
+// PAIRED (16-bit stores with the shifted copy, layered path): each x-neighbour
+// pair of a trilinear fetch is one 32-bit load (fetch_trilinear_pair, the same
+// values bit for bit), halving the gathers (survey layered composite 3.03 ->
+// 2.71 ms).  The independent partials march whole bricks without termination,
+// like MIP rays, and reading both copies there measured no faster (9.6-10.1 ->
+// 10.2 ms): they read the store alone.
+template <typename T, bool CARRIED, bool PAIRED>
 __global__ void __launch_bounds__(128)
 k_brick_partial(const __grid_constant__ SortParams P, int layer_begin, int layer_end) {
     __shared__ float4 s_tf[kMaxTF];
@@ -258,7 +264,12 @@ k_brick_partial(const __grid_constant__ SortParams P, int layer_begin, int layer
     const int end = P.sub_order ? P.sub_n : P.layer_start[layer_end];
     const int t0 = tile_start[first], t1 = tile_start[end];
     const T* __restrict__ pool = static_cast<const T*>(P.vol.pool);
+    const T* __restrict__ pool1 = static_cast<const T*>(P.vol.pool1);
     const float ert = P.ert;
+    auto fetch = [&](const T* slot, const T* slot1, float gx, float gy, float gz) {
+        if constexpr (PAIRED) return fetch_trilinear_pair<T>(slot, slot1, P.vol, gx, gy, gz);
+        else return fetch_trilinear<T>(slot, P.vol, gx, gy, gz);
+    };
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(P.work, 1);
@@ -297,11 +308,12 @@ k_brick_partial(const __grid_constant__ SortParams P, int layer_begin, int layer
         if (!CARRIED && P.mode == VR_MIP) {  // the brick's maximum (object-space MIP)
             float m = -INFINITY;
             if (any) {
-                const T* slot = pool + (long long)P.vol.table[b] * P.vol.slot_elems;
+                const long long base = (long long)P.vol.table[b] * P.vol.slot_elems;
+                const T* slot = pool + base;
+                const T* slot1 = PAIRED ? pool1 + base : nullptr;
                 for (int j = 0; j < kb - ka; ++j) {
                     const float fj = (float)j;
-                    m = fmaxf(m, fetch_trilinear<T>(slot, P.vol, fmaf(fj, e[0], g[0]), fmaf(fj, e[1], g[1]),
-                                                    fmaf(fj, e[2], g[2])));
+                    m = fmaxf(m, fetch(slot, slot1, fmaf(fj, e[0], g[0]), fmaf(fj, e[1], g[1]), fmaf(fj, e[2], g[2])));
                 }
             }
             const int rw = rect.z - rect.x + 1;
@@ -309,13 +321,14 @@ k_brick_partial(const __grid_constant__ SortParams P, int layer_begin, int layer
             continue;
         }
         if (any) {
-            const T* slot = pool + (long long)P.vol.table[b] * P.vol.slot_elems;
+            const long long base = (long long)P.vol.table[b] * P.vol.slot_elems;
+            const T* slot = pool + base;
+            const T* slot1 = PAIRED ? pool1 + base : nullptr;
             // at most ~4 B samples per brick: FP32 stepping from the float-float anchor
             // stays within 2e-5 voxel
             for (int j = 0; j < kb - ka; ++j) {
                 const float fj = (float)j;
-                const float v = fetch_trilinear<T>(slot, P.vol, fmaf(fj, e[0], g[0]), fmaf(fj, e[1], g[1]),
-                                                   fmaf(fj, e[2], g[2]));
+                const float v = fetch(slot, slot1, fmaf(fj, e[0], g[0]), fmaf(fj, e[1], g[1]), fmaf(fj, e[2], g[2]));
                 const float4 c = tf_lookup(s_tf, P.tf.n, P.tf.vmin, P.tf.inv_range, v);
                 const float w = Tr * c.w;
                 C0 = fmaf(w, c.x, C0);
@@ -421,7 +434,13 @@ __global__ void k_state_finish(const __grid_constant__ SortParams P) {
 
 template <typename T, bool CARRIED>
 cudaError_t partial_t(const SortParams& p, int l0, int l1, int grid, cudaStream_t s) {
-    k_brick_partial<T, CARRIED><<<grid, 128, 0, s>>>(p, l0, l1);
+    if constexpr (sizeof(T) == 2 && CARRIED) {
+        if (p.vol.pool1) {
+            k_brick_partial<T, CARRIED, true><<<grid, 128, 0, s>>>(p, l0, l1);
+            return cudaGetLastError();
+        }
+    }
+    k_brick_partial<T, CARRIED, false><<<grid, 128, 0, s>>>(p, l0, l1);
     return cudaGetLastError();
 }
 
