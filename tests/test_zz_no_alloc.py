@@ -56,6 +56,11 @@ def test_noalloc_matches_vr_render_on_consecutive_calls():
                 hit = torch.isfinite(ref_max)
                 assert torch.equal(torch.isfinite(mx), hit)
                 assert (mx[hit] - ref_max[hit]).abs().max().item() <= TOL * 10
+        # and the last call's image against the FP64 oracle on the same stored (FP16) values
+        from parity import compare
+        import oracle
+        sc = oracle.Scene(oracle.round_storage(vol, "f16"), synth.viridis_ramp_tf(), -1.0, 20.0, 0.5, 0.99)
+        compare(out[0].cpu().numpy().reshape(-1, 4), sc, cam, "mip", tol=TOL, path="brick")
     r.close()
 
 
