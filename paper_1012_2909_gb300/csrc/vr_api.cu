@@ -1091,6 +1091,8 @@ vr_status ensure_resident(vr_ctx* ctx, const int* list, int n, cudaStream_t s) {
 }
 
 // Footprints and visibility order of one camera (read back to the host).
+// Footprints, keys and visibility layers of every brick for camera cd, read back to the
+// host (the out-of-core batches and the distributed partials are planned from them).
 vr_status ooc_footprints(vr_ctx* ctx, const CamDev& cd, SortParams& sp, std::vector<int>& order,
                          std::vector<int>& layer_start, std::vector<BrickFoot>& foot, cudaStream_t s) {
     const long long nbricks = (long long)ctx->nbx * ctx->nby * ctx->nbz;
@@ -1102,18 +1104,18 @@ vr_status ooc_footprints(vr_ctx* ctx, const CamDev& cd, SortParams& sp, std::vec
         ctx->order = nullptr;
         ctx->tile_start = nullptr;
         ctx->sort_bricks = 0;
-        VR_CK(cudaMalloc(&ctx->foot, sizeof(BrickFoot) * (size_t)nbricks), "out of core: scratch");
-        VR_CK(cudaMalloc(&ctx->order, sizeof(int) * (size_t)nbricks), "out of core: scratch");
-        VR_CK(cudaMalloc(&ctx->tile_start, sizeof(int) * (size_t)(nbricks + 1)), "out of core: scratch");
+        VR_CK(cudaMalloc(&ctx->foot, sizeof(BrickFoot) * (size_t)nbricks), "footprints: scratch");
+        VR_CK(cudaMalloc(&ctx->order, sizeof(int) * (size_t)nbricks), "footprints: scratch");
+        VR_CK(cudaMalloc(&ctx->tile_start, sizeof(int) * (size_t)(nbricks + 1)), "footprints: scratch");
         ctx->sort_bricks = nbricks + 1;
     }
-    if (!ctx->partial_used) VR_CK(cudaMalloc(&ctx->partial_used, sizeof(unsigned long long)), "out of core: scratch");
+    if (!ctx->partial_used) VR_CK(cudaMalloc(&ctx->partial_used, sizeof(unsigned long long)), "footprints: scratch");
     const int L = layer_bound(ctx, cd);
     if (L + 1 > ctx->layer_cap) {
         if (ctx->layer_buf) cudaFree(ctx->layer_buf);
         ctx->layer_buf = nullptr;
         ctx->layer_cap = 0;
-        VR_CK(cudaMalloc(&ctx->layer_buf, sizeof(int) * 3 * (size_t)(L + 1)), "out of core: scratch");
+        VR_CK(cudaMalloc(&ctx->layer_buf, sizeof(int) * 3 * (size_t)(L + 1)), "footprints: scratch");
         ctx->layer_cap = L + 1;
     }
     if (!cam_ff(cd, sp.cam)) return fail(ctx, VR_ERR_INVALID_ARG, "vr_render: camera basis is singular");
@@ -1128,20 +1130,20 @@ vr_status ooc_footprints(vr_ctx* ctx, const CamDev& cd, SortParams& sp, std::vec
     sp.layer_count = ctx->layer_buf;
     sp.layer_start = ctx->layer_buf + (L + 1);
     sp.layer_fill = ctx->layer_buf + 2 * (L + 1);
-    VR_CK(cudaMemsetAsync(sp.layer_count, 0, sizeof(int) * (size_t)L, s), "out of core: reset");
-    VR_CK(cudaMemsetAsync(sp.partial_used, 0, sizeof(unsigned long long), s), "out of core: reset");
-    VR_CK(launch_brick_footprints(sp, s), "out of core: footprints");
+    VR_CK(cudaMemsetAsync(sp.layer_count, 0, sizeof(int) * (size_t)L, s), "footprints: reset");
+    VR_CK(cudaMemsetAsync(sp.partial_used, 0, sizeof(unsigned long long), s), "footprints: reset");
+    VR_CK(launch_brick_footprints(sp, s), "footprints: launch");
     layer_start.resize((size_t)L + 1);
     VR_CK(cudaMemcpyAsync(layer_start.data(), sp.layer_start, sizeof(int) * (size_t)(L + 1), cudaMemcpyDeviceToHost, s),
-          "out of core: read-back");
-    VR_CK(cudaStreamSynchronize(s), "out of core: read-back");
+          "footprints: read-back");
+    VR_CK(cudaStreamSynchronize(s), "footprints: read-back");
     const int nvis = layer_start[(size_t)L];
     order.resize((size_t)nvis);
     foot.resize((size_t)nbricks);
     if (nvis > 0) {
-        VR_CK(cudaMemcpy(order.data(), sp.order, sizeof(int) * (size_t)nvis, cudaMemcpyDeviceToHost), "out of core: read-back");
+        VR_CK(cudaMemcpy(order.data(), sp.order, sizeof(int) * (size_t)nvis, cudaMemcpyDeviceToHost), "footprints: read-back");
         VR_CK(cudaMemcpy(foot.data(), sp.foot, sizeof(BrickFoot) * (size_t)nbricks, cudaMemcpyDeviceToHost),
-              "out of core: read-back");
+              "footprints: read-back");
     }
     return VR_OK;
 }
@@ -1757,7 +1759,7 @@ vr_status dist_checks(vr_ctx* ctx, vr_mode mode, const char* what) {
 }
 
 vr_status dist_scratch(vr_ctx* ctx, long long nbricks) {
-    if (nbricks * 3 + 2 <= ctx->dist_cap * 3 + 2 && ctx->dist_ids) return VR_OK;
+    if (ctx->dist_ids && nbricks <= ctx->dist_cap) return VR_OK;
     if (ctx->dist_ids) cudaFree(ctx->dist_ids);
     if (ctx->dist_foot) cudaFree(ctx->dist_foot);
     ctx->dist_ids = nullptr;

@@ -117,24 +117,29 @@ class TorchTransport:
         table = [t.cpu().numpy() for t in table]  # table[s][d] = what s sends to d
         reqs, incoming = [], [None] * world
         recv_h, recv_p = {}, {}
+        # every rank knows every count, so empty messages are simply not sent
         for s in range(world):
             if s == me:
                 continue
             nh, npx = (int(v) for v in table[s][me])
             recv_h[s] = torch.zeros((nh, HEADER), dtype=torch.int64, device=dev)
             recv_p[s] = torch.zeros((npx, 4), dtype=torch.float32, device=dev)
-            reqs.append(dist.irecv(recv_h[s], src=s, group=self.group))
-            reqs.append(dist.irecv(recv_p[s], src=s, group=self.group))
+            if nh:
+                reqs.append(dist.irecv(recv_h[s], src=s, group=self.group))
+            if npx:
+                reqs.append(dist.irecv(recv_p[s], src=s, group=self.group))
         sends = []
         for d in range(world):
             if d == me:
                 continue
             h, p = outgoing[d]
             th = torch.as_tensor(h, dtype=torch.int64).reshape(-1, HEADER).to(dev).contiguous()
-            sends.append(th)
-            sends.append(p.contiguous())
-            reqs.append(dist.isend(sends[-2], dst=d, group=self.group))
-            reqs.append(dist.isend(sends[-1], dst=d, group=self.group))
+            tp = p.contiguous()
+            sends += [th, tp]
+            if th.shape[0]:
+                reqs.append(dist.isend(th, dst=d, group=self.group))
+            if tp.shape[0]:
+                reqs.append(dist.isend(tp, dst=d, group=self.group))
         for q in reqs:
             q.wait()
         for s in range(world):

@@ -111,7 +111,7 @@ def _worker(rank, world, port, q):
     q.put((rank, out))
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 4])  # 4 ranks over 3 brick layers: one rank holds no brick
 def test_exchange_and_fold_equal_the_oracle_sortlast(world):
     import oracle
     from paper_1012_2909_gb300 import dist
