@@ -465,7 +465,6 @@ __device__ __forceinline__ void march_segments(const BrickParams& P, const T* ti
                                                int nlong, int nshort, int* claim, int lane) {
     constexpr int PER_WARP = 32 / G;
     const int q = lane / G, r = lane % G;
-    const unsigned int gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (q * G);
     // batches never mix the lists: the long list is padded to whole batches
     const int nlong_pad = (nlong + PER_WARP - 1) / PER_WARP * PER_WARP;
     for (;;) {
@@ -485,7 +484,10 @@ __device__ __forceinline__ void march_segments(const BrickParams& P, const T* ti
             m = group_max<T, G, U, false>(tile, s, n, r, iters);
         else
             m = group_max<T, G, U, true>(tile, s, n, r, iters);
-        const unsigned int e = __reduce_max_sync(gmask, ord_enc(m));
+        // maximum over the group's G lanes: xor shuffles stay inside aligned groups
+        unsigned int e = ord_enc(m);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
         if (r == 0 && j0 + q < nseg) atomicMax(&P.out_enc[s.pix], e);
     }
 }
