@@ -677,7 +677,7 @@ def run_ours(a):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": f"{a.storage} storage, f32 arithmetic",
         "storage_dtype": a.storage,
         "data": "synthetic",
         "config": workload_config(a.storage, world),
