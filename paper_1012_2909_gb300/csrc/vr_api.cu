@@ -66,6 +66,9 @@ struct vr_ctx {
     // brick pass: TMA descriptor of the brick store
     CUtensorMap tmap;
     bool has_tmap = false;
+    // the sort-last partial pass: the same store with the box of brick_part_box_dims
+    CUtensorMap tmap_part;
+    bool has_tmap_part = false;
     vr_path path = VR_PATH_AUTO;
     vr_tuning tune{8, 4, 256, 8};  // tile_w, tile_h, block, group
     bool graph_mode = false;
@@ -240,6 +243,14 @@ bool make_tensor_map(vr_ctx* c) {
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     c->has_tmap = (r == CUDA_SUCCESS);
+    c->has_tmap_part = false;
+    if (c->has_tmap) {
+        brick_part_box_dims(c->dtype, &bx, &by, &bz);
+        cuuint32_t pbox[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+        r = enc(&c->tmap_part, dt, 4, c->pool, dims, strides, pbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        c->has_tmap_part = (r == CUDA_SUCCESS);
+    }
     return c->has_tmap;
 }
 
@@ -871,6 +882,51 @@ int layer_bound(const vr_ctx* ctx, const CamDev& c) {
     return m + 1;
 }
 
+// Sort-last partial images of camera cd through staged cells (launch_cell_partials:
+// the bricks of brick_list, or every brick), into sp.partial [0, npartial) with
+// the footprints sp.foot.  *done = false, with nothing launched, when this form
+// does not apply (no cells, a table beyond kMaxPartTF entries, slot indices
+// beyond an int): the caller then marches whole bricks (launch_brick_partial).
+vr_status staged_partials(vr_ctx* ctx, const CamDev& cd, const SortParams& sp, int mode, const int* brick_list,
+                          int nlist, long long npartial, cudaStream_t s, bool* done) {
+    *done = false;
+    if (!ctx->has_tmap_part || !ctx->cells || (int)ctx->tf.size() > kMaxPartTF || npartial >= (long long)INT_MAX)
+        return VR_OK;
+    BrickParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.vol = sp.vol;
+    bp.cams[0] = sp.cam;
+    bp.ncams = 1;
+    bp.width = cd.width;
+    bp.height = cd.height;
+    split(ctx->opt.step, bp.step, bp.step_lo);
+    int c3[3];
+    brick_cell_dims(ctx->dtype, &c3[0], &c3[1], &c3[2]);
+    bp.ncells_x = ctx->B / c3[0];
+    bp.ncells_y = ctx->B / c3[1];
+    bp.ncells_z = ctx->B / c3[2];
+    bp.nbricks = ctx->nbx * ctx->nby * ctx->nbz;
+    bp.krange = ctx->krange;
+    bp.pixdir = ctx->pixdir;  // written by the pixel set-up of this view
+    bp.status = ctx->status_dev;
+    bp.work = ctx->work;
+    bp.brick_list = brick_list;
+    bp.nlist = nlist;
+    bp.foot = sp.foot;
+    bp.partial = sp.partial;
+    bp.key_persp = cd.type == 1;
+    for (int a = 0; a < 3; ++a) {
+        bp.eye_cell[a] = (int)std::max<double>(-(1 << 20), std::min<double>(1 << 20, std::floor(cd.eye[a] / c3[a])));
+        bp.key_sign[a] = sp.cam.dir_hi[a] > 0.f ? 1 : (sp.cam.dir_hi[a] < 0.f ? -1 : 0);
+    }
+    VR_CK(launch_cell_partials(&ctx->tmap_part, bp, sp.tf, ctx->dtype, mode, npartial,
+                               cell_partial_passes(ctx->dtype, ctx->B), 2 * ctx->num_sms, ctx->cells, s,
+                               ctx->tune.group),
+          "sort-last partial images");
+    *done = true;
+    return VR_OK;
+}
+
 // Composite in object order.  carried = false: per-brick partial images from
 // T = 1 folded in visibility order (no early termination).  carried = true:
 // one visibility layer of bricks per launch, each pixel's running (C, T)
@@ -920,6 +976,7 @@ vr_status render_bricks_composite(vr_ctx* ctx, float* out_rgba, cudaStream_t s, 
     pp.width = W;
     pp.height = H;
     pp.krange = ctx->krange;
+    pp.pixdir = ctx->pixdir;
     pp.enc = ctx->enc;
     const int grid = ctx->num_sms * 8;
     for (size_t ci = 0; ci < ctx->cams.size(); ++ci) {
@@ -964,13 +1021,20 @@ vr_status render_bricks_composite(vr_ctx* ctx, float* out_rgba, cudaStream_t s, 
             if (g != VR_OK) return g;
             sp.partial = ctx->partial;
             sp.work = ctx->work;
-            VR_CK(cudaMemsetAsync(sp.work, 0, sizeof(int), s), "vr_render: scheduler reset");
             if (ctx->ev_start && ci == 0) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
-            VR_CK(launch_brick_partial(sp, ctx->dtype, false, 0, L, grid, s), "vr_render: partial images");
+            bool staged = false;
+            st = staged_partials(ctx, cd, sp, VR_COMPOSITE, nullptr, 0, (long long)used, s, &staged);
+            if (st != VR_OK) return st;
+            if (!staged) {
+                VR_CK(launch_tile_scan(sp, s), "vr_render: tile prefix");
+                VR_CK(cudaMemsetAsync(sp.work, 0, sizeof(int), s), "vr_render: scheduler reset");
+                VR_CK(launch_brick_partial(sp, ctx->dtype, false, 0, L, grid, s), "vr_render: partial images");
+            }
             if (ctx->ev_stop && ci + 1 == ctx->cams.size())
                 VR_CK(cudaEventRecord(ctx->ev_stop, s), "vr_render: profiling event");
             VR_CK(launch_sortlast_fold(sp, s), "vr_render: sort-last fold");
         } else {
+            VR_CK(launch_tile_scan(sp, s), "vr_render: tile prefix");
             VR_CK(launch_state_init(sp, s), "vr_render: state init");
             int slot = 0;
             if (ctx->ev_start && ci == 0) VR_CK(cudaEventRecord(ctx->ev_start, s), "vr_render: profiling event");
@@ -1818,6 +1882,7 @@ vr_status vr_sortlast_partials(vr_ctx* ctx, vr_mode mode, const int32_t* bricks,
     pp.width = W;
     pp.height = H;
     pp.krange = ctx->krange;
+    pp.pixdir = ctx->pixdir;
     pp.enc = ctx->enc;
     pp.cam = ray_cam(cd);
     VR_CK(launch_pixel_setup(pp, s), "vr_sortlast_partials: pixel set-up");
@@ -1867,8 +1932,14 @@ vr_status vr_sortlast_partials(vr_ctx* ctx, vr_mode mode, const int32_t* bricks,
     sp.sub_n = (int)sub.size();
     sp.partial = reinterpret_cast<float4*>(partial);
     sp.work = ctx->work;
-    VR_CK(cudaMemsetAsync(sp.work, 0, sizeof(int), s), "vr_sortlast_partials: scheduler reset");
-    VR_CK(launch_brick_partial(sp, ctx->dtype, false, 0, 0, ctx->num_sms * 8, s), "vr_sortlast_partials: partials");
+    bool staged = false;
+    st = staged_partials(ctx, cd, sp, mode, d_sub, (int)sub.size(), off, s, &staged);
+    if (st != VR_OK) return st;
+    if (!staged) {
+        VR_CK(cudaMemsetAsync(sp.work, 0, sizeof(int), s), "vr_sortlast_partials: scheduler reset");
+        VR_CK(launch_brick_partial(sp, ctx->dtype, false, 0, 0, ctx->num_sms * 8, s),
+              "vr_sortlast_partials: partials");
+    }
     // the host vectors are read by the copies above before the call returns
     VR_CK(cudaStreamSynchronize(s), "vr_sortlast_partials: upload");
     return VR_OK;

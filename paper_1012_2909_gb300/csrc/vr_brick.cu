@@ -118,8 +118,9 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
 
 // Trilinear fetch from a staged cell; g in tile coordinates (lower corner
 // floor(g), 0 = ghost).  CLAMP keeps every access inside the tile; without it
-// the caller guarantees 0 <= g < extent + 1 on every axis.
-template <typename T, bool CLAMP>
+// the caller guarantees 0 <= g < extent + 1 on every axis.  BY: rows of a slab
+// of the staged box.
+template <typename T, bool CLAMP, int BY = Cell<T>::BY>
 __device__ __forceinline__ float tile_fetch(const T* __restrict__ t, float gx, float gy, float gz) {
     using C = Cell<T>;
     if (CLAMP) {
@@ -129,8 +130,8 @@ __device__ __forceinline__ float tile_fetch(const T* __restrict__ t, float gx, f
     }
     const float x0 = floorf(gx), y0 = floorf(gy), z0 = floorf(gz);
     const float fx = gx - x0, fy = gy - y0, fz = gz - z0;
-    const int i = (int)fmaf(fmaf(z0, (float)C::BY, y0), (float)C::BX, x0);
-    constexpr int SY = C::BX, SZ = C::BX * C::BY;
+    const int i = (int)fmaf(fmaf(z0, (float)BY, y0), (float)C::BX, x0);
+    constexpr int SY = C::BX, SZ = C::BX * BY;
     const float c000 = cvt<T>(t[i]), c010 = cvt<T>(t[i + SY]);
     const float c001 = cvt<T>(t[i + SZ]), c011 = cvt<T>(t[i + SZ + SY]);
     const float a0 = fmaf(fx, sub_wide<T>(t[i + 1], c000), c000);
@@ -207,6 +208,30 @@ __device__ bool unit_cell(const BrickParams& P, int u, float3& lo, int4& coord) 
     lo = make_float3((float)ox, (float)oy, (float)oz);
     coord = make_int4(cx * C::CX, cy * C::CY, cz * C::CZ, v.table[brick]);
     return coord.w >= 0;
+}
+
+// Local visibility key of the cell of unit u (TMA coordinates coord) within its
+// brick, as BrickParams describes: it grows along every ray, and no ray crosses
+// two cells of one brick with the same key.
+template <typename T>
+__device__ int cell_key(const BrickParams& P, int u, int4 coord) {
+    using C = Cell<T>;
+    const VolDev& v = P.vol;
+    const int brick = u / (P.ncells_x * P.ncells_y * P.ncells_z);
+    const int b3[3] = {brick % v.nbx, (brick / v.nbx) % v.nby, brick / (v.nbx * v.nby)};
+    const int nc[3] = {P.ncells_x, P.ncells_y, P.ncells_z};
+    const int c3[3] = {coord.x / C::CX, coord.y / C::CY, coord.z / C::CZ};
+    int key = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (P.key_persp) {
+            const int lo = b3[a] * nc[a], hi = lo + nc[a] - 1, e = P.eye_cell[a];
+            key += abs(lo + c3[a] - e) - max(0, max(lo - e, e - hi));
+        } else {
+            key += P.key_sign[a] > 0 ? c3[a] : (P.key_sign[a] < 0 ? nc[a] - 1 - c3[a] : 0);
+        }
+    }
+    return key;
 }
 
 template <typename T>
@@ -335,7 +360,7 @@ __device__ __forceinline__ bool make_segment(const BrickParams& P, const CamFF& 
 }
 
 struct CellDesc {
-    float4 lo;    // lower corner (world voxels)
+    float4 lo;    // lower corner (world voxels); w: the brick id (int bits)
     int4 coord;   // TMA coordinates x, y, z (slot elements), slot
     int4 rect0;   // pixel rectangle of camera 0 (empty: x > z)
 };
@@ -356,6 +381,7 @@ __global__ void k_cell_list(const __grid_constant__ BrickParams P, CellDesc* __r
         float3 lo;
         int4 coord;
         bool ok = u0 + threadIdx.x < nunits && unit_cell<T>(P, u, lo, coord);
+        if (ok && P.key_pass > 0) ok = cell_key<T>(P, u, coord) == P.key_pass - 1;
         int4 rect0 = make_int4(0, 0, -1, -1);
         if (ok) {
             bool any = cam_cell_rect<T>(P.cams[0], lo, rect0);
@@ -372,7 +398,7 @@ __global__ void k_cell_list(const __grid_constant__ BrickParams P, CellDesc* __r
         base = __shfl_sync(0xffffffffu, base, 0);
         if (ok) {
             CellDesc d;
-            d.lo = make_float4(lo.x, lo.y, lo.z, 0.f);
+            d.lo = make_float4(lo.x, lo.y, lo.z, __int_as_float(u / ncells));
             d.coord = coord;
             d.rect0 = rect0;
             list[base + __popc(m & ((1u << lane) - 1u))] = d;
@@ -639,6 +665,327 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
     }
 }
 
+// ---------------------------------------------------------------------------
+// Sort-last partial images through staged cells.
+//
+// The partial image of a brick holds, per pixel, the "over" composite from T = 1
+// of the ray's samples that the brick owns (the maximum of their values for
+// MIP).  The brick's cells split those samples by the same face-crossing rule,
+// so the partial is the front-to-back fold of the pixel's cell segments.  Each
+// visibility pass stages the cells of one local key (k_cell_list), marches each
+// segment with G lanes on contiguous runs of samples, joins the runs in ray
+// order, and folds the segment into the brick's slot: C += T C_seg, T *= T_seg
+// (or the maximum).  Slots start as the empty image (0, 0, 0, 1), or -inf.
+
+// Staged box without the spare row (the partial pass also holds the table).
+template <typename T> struct PartGeom {
+    static constexpr int BY = Cell<T>::CY + 2;
+    static constexpr int BYTES = Cell<T>::BX * BY * Cell<T>::BZ * (int)sizeof(T);
+    static constexpr int STRIDE = (BYTES + 127) / 128 * 128;
+    static constexpr int SMEM = STRIDE + kSegCap * (int)sizeof(SegRec) + kMaxPartTF * (int)sizeof(float4);
+};
+
+// Segment records of one chunk of a cell's pixel rectangle, each pointing at its
+// slot in the partial image of the cell's brick (foot).  Records of at most
+// kShortRounds group rounds fill the buffer from the back, as in the MIP pass.
+template <typename T, int G>
+__device__ __forceinline__ void build_part_segments(const BrickParams& P, int4 rect, const BrickFoot& f, float3 lo,
+                                                    int c0, SegRec* segs, int* cnt, int tid) {
+    const CamFF& c = P.cams[0];
+    const int rw = rect.z - rect.x + 1;
+    const int npx = rw * (rect.w - rect.y + 1);
+    const int c1 = min(npx, c0 + kSegCap);
+    const float inv_rw = 1.0f / (float)rw;
+    const int frw = f.rect.z - f.rect.x + 1;
+    constexpr int PER = kSegCap / kBrickThreads;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int i = c0 + tid + q * kBrickThreads;
+        if (i >= c1) continue;
+        int row = (int)(((float)i + 0.5f) * inv_rw), col = i - row * rw;
+        if (col < 0) {
+            --row;
+            col += rw;
+        } else if (col >= rw) {
+            ++row;
+            col -= rw;
+        }
+        const int py = rect.y + row, px = rect.x + col;
+        // a pixel with a sample in the cell lies in its brick's rectangle
+        if (px < f.rect.x || px > f.rect.z || py < f.rect.y || py > f.rect.w) continue;
+        const long long pix = (long long)py * P.width + px;
+        const int2 kr = P.krange[pix];
+        if (kr.x >= kr.y) continue;
+        const float4* pd = P.pixdir ? P.pixdir + 2 * pix : nullptr;
+        SegRec s;
+        if (make_segment<T>(P, c, px, py, kr, lo, pd, s)) {
+            s.pix = (int)(f.offset + (long long)(py - f.rect.y) * frw + (px - f.rect.x));
+            if ((s.n & 0x7fffffff) > kShortRounds * G)
+                segs[atomicAdd(&cnt[0], 1)] = s;
+            else
+                segs[kSegCap - 1 - atomicAdd(&cnt[1], 1)] = s;
+        }
+    }
+}
+
+// One lane's contiguous run of a segment, samples [k0, k0 + L) clipped to n,
+// composited from T = 1 (the warp's lanes all take `iters` steps; steps past the
+// run add nothing: alpha 0 leaves C and T exactly as they are).
+template <typename T, bool CLAMP>
+__device__ __forceinline__ void run_over(const T* __restrict__ tile, const float4* __restrict__ s_tf, const TFDev& tf,
+                                         const SegRec& s, int n, int k0, int L, int iters, float& C0, float& C1,
+                                         float& C2, float& Tr) {
+    C0 = C1 = C2 = 0.f;
+    Tr = 1.f;
+    const float last = (float)(n - 1);
+    for (int j = 0; j < iters; ++j) {
+        const int k = k0 + j;
+        const float f = fminf((float)k, last);
+        const float v = tile_fetch<T, CLAMP, PartGeom<T>::BY>(tile, fmaf(f, s.ex, s.gx), fmaf(f, s.ey, s.gy),
+                                                              fmaf(f, s.ez, s.gz));
+        const float4 c = tf_lookup(s_tf, tf.n, tf.vmin, tf.inv_range, v);
+        const float a = (j < L && k < n) ? c.w : 0.f;
+        const float w = Tr * a;
+        C0 = fmaf(w, c.x, C0);
+        C1 = fmaf(w, c.y, C1);
+        C2 = fmaf(w, c.z, C2);
+        Tr = Tr * (1.f - a);
+    }
+}
+
+// Maximum over a segment, lane r on samples r, r + G, ... (repeats of the last
+// sample change nothing).
+template <typename T, int G, bool CLAMP>
+__device__ __forceinline__ float run_max(const T* __restrict__ tile, const SegRec& s, int n, int r, int iters) {
+    float m = -INFINITY;
+    const float last = (float)(n - 1);
+    float fr = (float)r;
+    for (int it = 0; it < iters; ++it, fr += (float)G) {
+        const float f = fminf(fr, last);
+        m = fmaxf(m, tile_fetch<T, CLAMP, PartGeom<T>::BY>(tile, fmaf(f, s.ex, s.gx), fmaf(f, s.ey, s.gy),
+                                                            fmaf(f, s.ez, s.gz)));
+    }
+    return m;
+}
+
+// Warps claim batches of 32 / G records (as in march_segments); each group of G
+// lanes marches one record and its lane 0 folds the result into the record's
+// slot.  A pass never holds two records of one slot.
+template <typename T, int MODE, int G>
+__device__ __forceinline__ void march_part(const BrickParams& P, const T* tile, const float4* s_tf, const TFDev& tf,
+                                           const SegRec* segs, int nlong, int nshort, int* claim, int lane) {
+    constexpr int PER_WARP = 32 / G;
+    const int q = lane / G, r = lane % G;
+    const int nlong_pad = (nlong + PER_WARP - 1) / PER_WARP * PER_WARP;
+    for (;;) {
+        int s0 = 0;
+        if (lane == 0) s0 = atomicAdd(claim, PER_WARP);
+        s0 = __shfl_sync(0xffffffffu, s0, 0);
+        if (s0 >= nlong_pad + nshort) break;
+        const bool in_long = s0 < nlong_pad;
+        const int j0 = in_long ? s0 : s0 - nlong_pad, nseg = in_long ? nlong : nshort;
+        const int j = min(j0 + q, nseg - 1);
+        const SegRec s = segs[in_long ? j : kSegCap - 1 - j];
+        const int n = s.n & 0x7fffffff;
+        const bool writer = r == 0 && j0 + q < nseg;  // groups past the list's end repeat its last record
+        const bool clamp = __any_sync(0xffffffffu, s.n < 0);
+        if (MODE == VR_MIP) {
+            const int iters = (int)__reduce_max_sync(0xffffffffu, (unsigned int)((n + G - 1) / G));
+            float m = clamp ? run_max<T, G, true>(tile, s, n, r, iters) : run_max<T, G, false>(tile, s, n, r, iters);
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (writer) {
+                float4* d = P.partial + s.pix;
+                d->x = fmaxf(d->x, m);
+            }
+        } else {
+            const int L = (n + G - 1) / G;  // samples per lane: lane r takes [r L, r L + L)
+            const int iters = (int)__reduce_max_sync(0xffffffffu, (unsigned int)L);
+            float C0, C1, C2, Tr;
+            if (clamp)
+                run_over<T, true>(tile, s_tf, tf, s, n, r * L, L, iters, C0, C1, C2, Tr);
+            else
+                run_over<T, false>(tile, s_tf, tf, s, n, r * L, L, iters, C0, C1, C2, Tr);
+            // join the runs in ray order: (C, T) of lanes r and r + d, then r and r + 2d, ...
+#pragma unroll
+            for (int d = 1; d < G; d <<= 1) {
+                const float p0 = __shfl_down_sync(0xffffffffu, C0, d, G);
+                const float p1 = __shfl_down_sync(0xffffffffu, C1, d, G);
+                const float p2 = __shfl_down_sync(0xffffffffu, C2, d, G);
+                const float pT = __shfl_down_sync(0xffffffffu, Tr, d, G);
+                if ((r & (2 * d - 1)) == 0) {
+                    C0 = fmaf(Tr, p0, C0);
+                    C1 = fmaf(Tr, p1, C1);
+                    C2 = fmaf(Tr, p2, C2);
+                    Tr *= pT;
+                }
+            }
+            if (writer) {
+                float4 p = P.partial[s.pix];
+                p.x = fmaf(p.w, C0, p.x);
+                p.y = fmaf(p.w, C1, p.y);
+                p.z = fmaf(p.w, C2, p.z);
+                p.w *= Tr;
+                P.partial[s.pix] = p;
+            }
+        }
+    }
+}
+
+// One pass of the sort-last partials: two CTAs per SM, one staged cell each
+// (the same claim / stage / build pipeline as k_brick_mip, one camera).
+template <typename T, int MODE, int GROUP>
+__global__ void __launch_bounds__(kBrickThreads, 2)
+k_cell_partial(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ BrickParams P,
+               const __grid_constant__ TFDev tf, const CellDesc* __restrict__ list, const int* __restrict__ count) {
+    using PG = PartGeom<T>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    T* tile = reinterpret_cast<T*>(smem);
+    SegRec* segs = reinterpret_cast<SegRec*>(smem + PG::STRIDE);
+    float4* s_tf = reinterpret_cast<float4*>(smem + PG::STRIDE + kSegCap * sizeof(SegRec));
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ CellDesc s_desc[3];
+    __shared__ BrickFoot s_foot[3];
+    __shared__ int s_u[3];
+    __shared__ int s_cnt[2][2];
+    __shared__ int s_claim[2];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nvalid = *count;
+    if (MODE == VR_COMPOSITE)
+        for (int i = tid; i < tf.n; i += kBrickThreads) s_tf[i] = tf.tab[i];
+    // warp 0: claim the next unit into descriptor slot `slot` (returns the unit)
+    auto claim = [&](int slot) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(P.work, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (lane == 0) {
+            s_u[slot] = u;
+            if (u < nvalid) {
+                const CellDesc d = list[u];
+                s_desc[slot] = d;
+                s_foot[slot] = P.foot[__float_as_int(d.lo.w)];
+            }
+        }
+        return u;
+    };
+    auto load = [&](const CellDesc& d) {  // thread 0: stage a cell
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar, (uint32_t)PG::BYTES);
+        tma_load_4d(tile, &tmap, &bar, d.coord.x, d.coord.y, d.coord.z, d.coord.w);
+    };
+    auto npx_of = [&](int slot) {
+        const int4 r = s_desc[slot].rect0;
+        return (r.z - r.x + 1) * (r.w - r.y + 1);  // listed cells have a non-empty rectangle
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_init(&bar, 1);
+            fence_mbar_init();
+            s_cnt[0][0] = s_cnt[0][1] = 0;
+            s_cnt[1][0] = s_cnt[1][1] = 0;
+            s_claim[0] = 0;
+        }
+        if (claim(0) < nvalid) {
+            __syncwarp();
+            if (lane == 0) load(s_desc[0]);
+            claim(1);
+        }
+    }
+    __syncthreads();
+    if (s_u[0] >= nvalid) return;
+
+    int cur = 0, chunk = 0, c0 = 0;
+    uint32_t phase = 0;
+    float3 lo = make_float3(s_desc[cur].lo.x, s_desc[cur].lo.y, s_desc[cur].lo.z);
+    build_part_segments<T, GROUP>(P, s_desc[cur].rect0, s_foot[cur], lo, c0, segs, s_cnt[0], tid);
+    bool ok = mbar_wait(&bar, phase, P.status);
+    phase ^= 1u;
+    // a failed wait (2 s without the copy completing) stops the CTA; the next call
+    // reports the status (the recovery assumes that the stalled copy never lands)
+    if (!__syncthreads_and(ok)) return;
+    for (;;) {
+        const int nlong = s_cnt[chunk & 1][0], nshort = s_cnt[chunk & 1][1];
+        if (tid == 0) {
+            s_cnt[(chunk + 1) & 1][0] = 0;
+            s_cnt[(chunk + 1) & 1][1] = 0;
+            s_claim[(chunk + 1) & 1] = 0;
+        }
+        march_part<T, MODE, GROUP>(P, tile, s_tf, tf, segs, nlong, nshort, &s_claim[chunk & 1], lane);
+        __syncthreads();
+        ++chunk;
+        c0 += kSegCap;
+        if (c0 < npx_of(cur)) {  // more pixels of the same cell
+            build_part_segments<T, GROUP>(P, s_desc[cur].rect0, s_foot[cur], lo, c0, segs, s_cnt[chunk & 1], tid);
+            __syncthreads();
+            continue;
+        }
+        const int nxt = cur == 2 ? 0 : cur + 1;
+        if (s_u[nxt] >= nvalid) break;
+        if (tid == 0) load(s_desc[nxt]);
+        cur = nxt;
+        c0 = 0;
+        lo = make_float3(s_desc[cur].lo.x, s_desc[cur].lo.y, s_desc[cur].lo.z);
+        build_part_segments<T, GROUP>(P, s_desc[cur].rect0, s_foot[cur], lo, c0, segs, s_cnt[chunk & 1], tid);
+        // the slot after `cur` was last read two units ago: refill it now
+        if (warp == 0) claim(cur == 2 ? 0 : cur + 1);
+        ok = mbar_wait(&bar, phase, P.status);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) return;
+    }
+}
+
+__global__ void k_fill_partial(float4* __restrict__ p, long long n, float4 v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+template <typename T, int MODE, int GROUP>
+cudaError_t launch_part(const void* tmap, const BrickParams& p, const TFDev& tf, int grid, const CellDesc* list,
+                        const int* count, cudaStream_t s) {
+    constexpr int SMEM = PartGeom<T>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_cell_partial<T, MODE, GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM);
+    if (e != cudaSuccess) return e;
+    k_cell_partial<T, MODE, GROUP><<<grid, kBrickThreads, SMEM, s>>>(*static_cast<const CUtensorMap*>(tmap), p, tf,
+                                                                      list, count);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cell_partials_t(const void* tmap, const BrickParams& p0, const TFDev& tf, int mode, long long npartial,
+                            int npass, int grid, void* cells, cudaStream_t s, int group) {
+    CellDesc* list = reinterpret_cast<CellDesc*>(static_cast<char*>(cells) + 256);
+    int* count = static_cast<int*>(cells);
+    const float4 empty = mode == VR_MIP ? make_float4(-INFINITY, 0.f, 0.f, 0.f) : make_float4(0.f, 0.f, 0.f, 1.f);
+    if (npartial > 0) {
+        k_fill_partial<<<(int)std::min<long long>((npartial + 255) / 256, 152 * 16), 256, 0, s>>>(p0.partial,
+                                                                                                  npartial, empty);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    BrickParams p = p0;
+    const int nunits = (p.brick_list ? p.nlist : p.nbricks) * p.ncells_x * p.ncells_y * p.ncells_z;
+    for (int pass = 0; pass < npass; ++pass) {
+        p.key_pass = pass + 1;
+        cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p.work, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        k_cell_list<T><<<std::min((nunits + 255) / 256, 4096), 256, 0, s>>>(p, list, count);
+        if (mode == VR_MIP)
+            e = group == 4    ? launch_part<T, VR_MIP, 4>(tmap, p, tf, grid, list, count, s)
+                : group == 16 ? launch_part<T, VR_MIP, 16>(tmap, p, tf, grid, list, count, s)
+                              : launch_part<T, VR_MIP, 8>(tmap, p, tf, grid, list, count, s);
+        else
+            e = group == 4    ? launch_part<T, VR_COMPOSITE, 4>(tmap, p, tf, grid, list, count, s)
+                : group == 16 ? launch_part<T, VR_COMPOSITE, 16>(tmap, p, tf, grid, list, count, s)
+                              : launch_part<T, VR_COMPOSITE, 8>(tmap, p, tf, grid, list, count, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 __global__ void k_pixel_setup(const __grid_constant__ PixelParams P) {
     const int n = P.width * P.height;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -722,6 +1069,32 @@ void brick_box_dims(vr_dtype dt, int* bx, int* by, int* bz) {
         *by = Cell<__half>::BY;
         *bz = Cell<__half>::BZ;
     }
+}
+
+void brick_part_box_dims(vr_dtype dt, int* bx, int* by, int* bz) {
+    if (dt == VR_F32) {
+        *bx = Cell<float>::BX;
+        *by = PartGeom<float>::BY;
+        *bz = Cell<float>::BZ;
+    } else {
+        *bx = Cell<__half>::BX;
+        *by = PartGeom<__half>::BY;
+        *bz = Cell<__half>::BZ;
+    }
+}
+
+int cell_partial_passes(vr_dtype dt, int brick) {
+    int cx, cy, cz;
+    brick_cell_dims(dt, &cx, &cy, &cz);
+    return brick / cx + brick / cy + brick / cz - 2;  // local keys 0 .. sum of (cells per axis - 1)
+}
+
+cudaError_t launch_cell_partials(const void* tmap, const BrickParams& p, const TFDev& tf, vr_dtype dt, int mode,
+                                 long long npartial, int npass, int grid, void* cells, cudaStream_t s, int group) {
+    if (tf.n > kMaxPartTF || !p.partial || !p.foot || !p.work) return cudaErrorInvalidValue;
+    if (dt == VR_F32) return cell_partials_t<float>(tmap, p, tf, mode, npartial, npass, grid, cells, s, group);
+    if (dt == VR_F16) return cell_partials_t<__half>(tmap, p, tf, mode, npartial, npass, grid, cells, s, group);
+    return cell_partials_t<__nv_bfloat16>(tmap, p, tf, mode, npartial, npass, grid, cells, s, group);
 }
 
 cudaError_t launch_pixel_setup(const PixelParams& p, cudaStream_t s) {

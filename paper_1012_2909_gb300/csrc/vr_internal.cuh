@@ -80,6 +80,8 @@ struct MarchParams {
 
 
 
+struct BrickFoot;
+
 // Launch parameters of the brick (object-order) pass for up to kMaxLaunchCams
 // cameras of one size; per-pixel arrays are camera-major (cam * W * H + pixel).
 struct BrickParams {
@@ -98,6 +100,18 @@ struct BrickParams {
     int nlist, pad_l;
     int* work;               // brick counter (zeroed)
     int* status;             // device status word (0 = ok)
+    // Sort-last partial images by staged cells (launch_cell_partials), camera 0 only.
+    // The cells of one brick are visited in passes of equal local visibility key:
+    // perspective key sum_a |c_a - eye_cell_a| minus its least value over the
+    // brick's cells; orthographic key sum_a of the cell index counted along the
+    // view direction's sign on that axis.  No ray crosses two cells of one brick
+    // with the same key, so the cells of a pass fold into disjoint pixels.
+    const BrickFoot* foot;   // per brick: rectangle and offset of its partial image
+    float4* partial;         // partial images: (C, T), or the maximum in .x (MIP)
+    int key_pass;            // k_cell_list keeps the cells of local key key_pass - 1 only (0: all cells)
+    int key_persp;           // 1: perspective key, 0: orthographic key
+    int eye_cell[3];         // perspective: floor(eye / cell edge) per axis, clamped
+    int key_sign[3];         // orthographic: sign of the view direction per axis
 };
 
 // Launch parameters of the adjoint (one batch of at most kMaxLaunchCams cameras).
@@ -181,13 +195,31 @@ cudaError_t launch_mip_finalize(const PixelParams& p, cudaStream_t s);
 cudaError_t launch_brick_mip(const void* tmap, const BrickParams& p, vr_dtype dt, int grid, void* cells,
                              cudaStream_t s, int group = 8);
 size_t brick_cells_bytes(long long nunits);
+// Sort-last partial images (the per-brick (C, T), or maxima for VR_MIP) of the
+// bricks p.brick_list (or every brick) for camera 0, through staged cells: the
+// partial slots [0, npartial) are first set to the empty image, then `npass`
+// visibility passes fold every cell segment into its brick's slot.  tmap is the
+// store's tensor map with the box brick_part_box_dims; tf must have at most
+// kMaxPartTF entries; every slot index must fit an int.
+constexpr int kMaxPartTF = 256;
+cudaError_t launch_cell_partials(const void* tmap, const BrickParams& p, const TFDev& tf, vr_dtype dt, int mode,
+                                 long long npartial, int npass, int grid, void* cells, cudaStream_t s,
+                                 int group = 8);
+// Number of visibility passes launch_cell_partials needs for a brick edge.
+int cell_partial_passes(vr_dtype dt, int brick);
+// TMA box of one cell for launch_cell_partials (no spare row), in elements.
+void brick_part_box_dims(vr_dtype dt, int* bx, int* by, int* bz);
 // Cell (staging unit) edge lengths for a storage type; the brick edge must be a
 // multiple of each.
 void brick_cell_dims(vr_dtype dt, int* cx, int* cy, int* cz);
 // TMA box of one cell (cell + 2 ghost, x padded to 16 bytes, one spare row for
 // 16-bit stores), in elements.
 void brick_box_dims(vr_dtype dt, int* bx, int* by, int* bz);
+// Footprints, keys and the visibility order of the bricks (p.order, p.layer_*).
 cudaError_t launch_brick_footprints(const SortParams& p, cudaStream_t s);
+// Prefix of the 8 x 4 pixel tiles of the ordered bricks (p.tile_start), for
+// launch_brick_partial over p.order.
+cudaError_t launch_tile_scan(const SortParams& p, cudaStream_t s);
 cudaError_t launch_brick_partial(const SortParams& p, vr_dtype dt, bool carried, int l0, int l1, int grid,
                                  cudaStream_t s);
 cudaError_t launch_sortlast_fold(const SortParams& p, cudaStream_t s);

@@ -6,9 +6,13 @@
 //
 //   * k_brick_footprints: per brick, its screen rectangle (projection of its
 //     box), its visibility key and a slice of a partial-image buffer;
-//   * k_brick_partial<INDEPENDENT>: per (brick, pixel of its rectangle), the
-//     "over" composite of the ray's samples owned by the brick, from T = 1,
-//     stored as (C, T) -- the brick's partial image;
+//   * the brick's partial image: per pixel of its rectangle, the "over"
+//     composite of the ray's samples owned by the brick, from T = 1, stored as
+//     (C, T).  It is computed through staged cells (launch_cell_partials in
+//     vr_brick.cu: the brick's cells in visibility passes, each cell segment
+//     folded into the brick's slot), or, for tables beyond that path's 256
+//     entries, by k_brick_partial<INDEPENDENT> marching whole bricks from
+//     global memory;
 //   * k_sortlast_fold: per pixel, the partial images folded front to back in
 //     visibility order (C += T C_b, T *= T_b);
 //   * with P.mode == VR_MIP the partial image of a brick is the maximum of its
@@ -455,8 +459,10 @@ cudaError_t launch_brick_footprints(const SortParams& p, cudaStream_t s) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_layer_scatter<<<std::min((nb + 255) / 256, 1024), 256, 0, s>>>(p);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scan(const SortParams& p, cudaStream_t s) {
     k_tile_scan<<<1, 32, 0, s>>>(p);
     return cudaGetLastError();
 }

@@ -377,7 +377,9 @@ def test_brick_path_rejects_composite_and_small_bricks(vr):
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_survey_workload_sampled_pixels(vr, storage):
     """Full-size 1024 x 1024 x 2048 cube (2000 sources + ripple), perspective 1920 x 1080,
-    two orbit frames; 4096 seeded pixels checked against the oracle."""
+    two orbit frames; 4096 seeded pixels checked against the oracle, for the image-order
+    composite and MIP, the brick-pass MIP and the sort-last composite (per-brick partial
+    images from staged cells, folded in visibility order; no termination)."""
     cfg = synth.CONFIGS["survey"]
     p = cfg["cube"]
     dims = (p["nx"], p["ny"], p["nz"])
@@ -403,6 +405,14 @@ def test_survey_workload_sampled_pixels(vr, storage):
             st = compare(img[i][pix], sc, c, mode, pixels=pix, tol=1e-4,
                          gpu_max=mxs[i][pix] if mode == "mip" else None, max_tol=2e-3, path=path)
             print(storage, mode, path, i, st)
+    sc_off = oracle.Scene(ref_vol, tf, -1.0, 20.0, 0.5, 2.0)
+    r.set_path("sortlast")
+    out = r.render("composite")
+    torch.cuda.synchronize()
+    img = out.cpu().numpy().reshape(2, -1, 4)
+    for i, c in enumerate(cams):
+        st = compare(img[i][pix], sc_off, c, "composite", pixels=pix, tol=1e-4, path="sortlast")
+        print(storage, "composite", "sortlast", i, st)
     r.close()
 
 
@@ -450,3 +460,13 @@ def test_sortlast_and_layered_composite(vr, storage):
         img, _ = _render(vr, vol, tf, cams, "composite", storage=storage, brick=brick, path="layered")
         for i, c in enumerate(cams):
             compare(img[i].reshape(-1, 4), sc_on, c, "composite", tol=1e-4, path="layered")
+    # a 1024-entry table: the partial images come from whole-brick marches instead of
+    # staged cells (whose shared copy of the table holds at most 256 entries)
+    dims, brick = (96, 80, 72), 32
+    vol = synth.generate(synth.cube_params(*dims, seed=249, nsrc=8, ripple=True, ripple_period=32.0))
+    tf = synth.viridis_ramp_tf(1024)
+    cams = [synth.orbit_view(dims, az, 53, 41) for az in (20.0, 200.0)]
+    img, _ = _render(vr, vol, tf, cams, "composite", storage=storage, brick=brick, path="sortlast")
+    sc_off = oracle.Scene(oracle.round_storage(vol, storage), tf, -1.0, 20.0, 0.5, 2.0)
+    for i, c in enumerate(cams):
+        compare(img[i].reshape(-1, 4), sc_off, c, "composite", tol=1e-4, path="sortlast")
