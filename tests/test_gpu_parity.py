@@ -460,6 +460,33 @@ def test_sortlast_and_layered_composite(vr, storage):
         img, _ = _render(vr, vol, tf, cams, "composite", storage=storage, brick=brick, path="layered")
         for i, c in enumerate(cams):
             compare(img[i].reshape(-1, 4), sc_on, c, "composite", tol=1e-4, path="layered")
+    # visibility passes of the staged cells at their edge cases: an orthographic view
+    # straight along z (two axes give equal keys), perspective eyes exactly on cell
+    # boundary planes (inside the cube and outside it), and a view that misses the cube
+    dims, brick = (130, 70, 200), 64
+    vol = synth.generate(synth.cube_params(*dims, seed=331, nsrc=8, ripple=True, ripple_period=32.0))
+    tf = synth.viridis_ramp_tf()
+
+    def aim(eye, target, w=53, h=41, fov=60.0):
+        f = np.asarray(target, np.float64) - np.asarray(eye, np.float64)
+        f /= np.linalg.norm(f)
+        right = np.cross((0.0, 1.0, 0.0), f)
+        right /= np.linalg.norm(right)
+        up = np.cross(f, right)
+        t = np.tan(np.radians(fov) / 2.0)
+        return dict(type=1, eye=[float(v) for v in eye], right=[float(v) for v in right],
+                    up=[float(v) for v in up], fwd=[float(v) for v in f],
+                    win=[-t * w / h, t * w / h, -t, t], width=w, height=h)
+
+    cams = [synth.ortho_view(dims, 53, 41, rx_deg=0.0, ry_deg=0.0),
+            aim((64.0, 32.0, 96.0), (10.0, 60.0, 190.0)),     # inside, on x, y and z cell planes
+            aim((64.0, 32.0, -160.0), (70.0, 40.0, 100.0)),   # outside, on x and y cell planes
+            aim((65.0, 35.0, 500.0), (65.0, 35.0, 900.0))]    # looks away: every ray misses
+    img, _ = _render(vr, vol, tf, cams, "composite", storage=storage, brick=brick, path="sortlast")
+    sc_off = oracle.Scene(oracle.round_storage(vol, storage), tf, -1.0, 20.0, 0.5, 2.0)
+    for i, c in enumerate(cams):
+        compare(img[i].reshape(-1, 4), sc_off, c, "composite", tol=1e-4, path="sortlast")
+    assert not img[3].any()
     # a 1024-entry table: the partial images come from whole-brick marches instead of
     # staged cells (whose shared copy of the table holds at most 256 entries)
     dims, brick = (96, 80, 72), 32
