@@ -92,26 +92,31 @@ def fold_order(foot):
 
 
 class TorchTransport:
-    """The exchange over a torch.distributed process group (gloo on CPU tensors, NCCL on
-    device tensors)."""
+    """The exchange over a torch.distributed process group: NCCL moves device tensors
+    directly; gloo moves host tensors, so device payloads are staged through host memory
+    (host_staging None: staged exactly when the group's backend is gloo) and handed back
+    on their device."""
 
-    def __init__(self, group=None):
+    def __init__(self, group=None, host_staging=None):
         import torch.distributed as dist
 
         self.dist = dist
         self.group = group
         self.rank = dist.get_rank(group)
         self.world = dist.get_world_size(group)
+        if host_staging is None:
+            host_staging = str(dist.get_backend(group)) == "gloo"
+        self.host_staging = bool(host_staging)
 
     def alltoall(self, outgoing):
         """outgoing[d] = (headers, payload) for rank d -> incoming[s] from rank s."""
         import torch
 
         dist, world, me = self.dist, self.world, self.rank
-        dev = outgoing[me][1].device
+        dev = outgoing[me][1].device  # where the payloads live and are handed back
+        comm = torch.device("cpu") if self.host_staging else dev  # where they travel
         counts = torch.tensor([[h.shape[0], p.shape[0]] for h, p in outgoing], dtype=torch.int64)
-        if dev.type == "cuda":
-            counts = counts.to(dev)
+        counts = counts.to(comm)
         table = [torch.zeros_like(counts) for _ in range(world)]
         dist.all_gather(table, counts, group=self.group)
         table = [t.cpu().numpy() for t in table]  # table[s][d] = what s sends to d
@@ -122,8 +127,8 @@ class TorchTransport:
             if s == me:
                 continue
             nh, npx = (int(v) for v in table[s][me])
-            recv_h[s] = torch.zeros((nh, HEADER), dtype=torch.int64, device=dev)
-            recv_p[s] = torch.zeros((npx, 4), dtype=torch.float32, device=dev)
+            recv_h[s] = torch.zeros((nh, HEADER), dtype=torch.int64, device=comm)
+            recv_p[s] = torch.zeros((npx, 4), dtype=torch.float32, device=comm)
             if nh:
                 reqs.append(dist.irecv(recv_h[s], src=s, group=self.group))
             if npx:
@@ -133,8 +138,8 @@ class TorchTransport:
             if d == me:
                 continue
             h, p = outgoing[d]
-            th = torch.as_tensor(h, dtype=torch.int64).reshape(-1, HEADER).to(dev).contiguous()
-            tp = p.contiguous()
+            th = torch.as_tensor(h, dtype=torch.int64).reshape(-1, HEADER).to(comm).contiguous()
+            tp = p.to(comm).contiguous()
             sends += [th, tp]
             if th.shape[0]:
                 reqs.append(dist.isend(th, dst=d, group=self.group))
@@ -146,7 +151,7 @@ class TorchTransport:
             if s == me:
                 incoming[s] = outgoing[me]
             else:
-                incoming[s] = (recv_h[s].cpu().numpy(), recv_p[s])
+                incoming[s] = (recv_h[s].cpu().numpy(), recv_p[s].to(dev))
         return incoming
 
 
