@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--cube", default=None,
                     help="NX,NY,NZ: override the cube size (same source density) for small captures")
     ap.add_argument("--frame", type=int, default=None, help="with --profile: render this frame only")
+    ap.add_argument("--ooc-full-mip", type=int, default=0,
+                    help="render this many full-view MIP frames of the out-of-core cube (minutes each) and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the wall / gradient / out-of-core measurements")
     return ap.parse_args()
@@ -450,6 +452,46 @@ def extra_ooc(dev, cache_gib=32, frames=10):
     callback), the host-to-device link (the bytes copied and their floor at the measured
     pinned copy rate), the host's waits on the device, and the rest; the frame's floor is
     its largest stage."""
+    import synth
+    r, frame, dims, W, H, h2d_gbs = _ooc_session(dev, cache_gib)
+    cams = synth.orbit(dims, frames, 10.0, W, H)
+    comp = [frame(c, "composite") for c in cams]
+    warm = frame(cams[-1], "composite")  # the last view again: everything cached
+    mip = []
+    for c in cams[:2]:
+        big = dict(c, width=W * 20, height=H * 20)
+        mip.append(frame(synth.wall_views(big, 20, 20)[210], "mip"))  # panel (10, 10) of 20 x 20
+    r.close()
+    tot = lambda xs, k: sum(x[k] for x in xs)  # noqa: E731
+    return {"workload": "4096x4096x8192 FP16 (256 GiB) streamed from the generator, 32 GiB cache, 1920x1080; "
+                        f"composite: {frames}-frame orbit (10 deg steps); MIP: central 1/400 panel of the "
+                        "view (bounded share of the cube), 2 orbit positions",
+            "h2d_link_gbs": h2d_gbs,
+            "composite_frames": comp, "composite_warm_repeat": warm, "mip_frames": mip,
+            "composite_orbit_s": tot(comp, "wall_s"), "composite_orbit_generate_s": tot(comp, "generate_s"),
+            "composite_orbit_floor_s": tot(comp, "floor_s"),
+            "mip_frame_s": [m["wall_s"] for m in mip], "mip_bricks": [m["bricks_fetched"] for m in mip],
+            "cold_frame_s": comp[0]["wall_s"], "warm_frame_s": warm["wall_s"],
+            "generate_gbs": tot(comp, "h2d_gb") / max(tot(comp, "generate_s"), 1e-9)}
+
+
+def run_ooc_full_mip(a):
+    """Full-view MIP frames of the out-of-core cube (every brick a ray crosses, about
+    275 GB of FP16 a frame, produced by the generator): minutes a frame, so a separate
+    run, not a bench extra.  Prints one JSON line with the stages of every frame."""
+    import synth
+    r, frame, dims, W, H, h2d_gbs = _ooc_session(0, 32)
+    cams = synth.orbit(dims, max(a.ooc_full_mip, 1), 10.0, W, H)
+    out = [frame(c, "mip") for c in cams]
+    r.close()
+    print(json.dumps({"ooc_full_mip": {"workload": "4096x4096x8192 FP16 (256 GiB) streamed from the generator, "
+                                                   "32 GiB cache, 1920x1080 full view, orbit positions 10 deg apart",
+                                       "h2d_link_gbs": h2d_gbs, "frames": out}}), flush=True)
+
+
+def _ooc_session(dev, cache_gib):
+    """The out-of-core cube loaded through the generator's region callback, with the
+    measured pinned host-to-device rate and a frame timer that separates the stages."""
     import torch
 
     import paper_1012_2909_gb300 as vr
@@ -466,6 +508,7 @@ def extra_ooc(dev, cache_gib=32, frames=10):
     torch.cuda.empty_cache()
     r = vr.Renderer(dev, brick=128, step=cfg["step"], ert=cfg["ert"])
     fn, user = synth.region_callback(p)
+    r.region_user = user  # the callback reads it at every render: keep it alive with the renderer
     vr.vr_load_cube_streamed(r.ctx, fn, user, dims, "f16", cache_bytes=cache_gib << 30)
     r.set_transfer_function(synth.viridis_ramp_tf(), -1.0, 20.0)
     W, H = cfg["image"]
@@ -488,25 +531,7 @@ def extra_ooc(dev, cache_gib=32, frames=10):
                 "floor_s": max(stages["generate_s"], link), "wall_over_floor": wall / max(1e-9, max(
                     stages["generate_s"], link))}
 
-    cams = synth.orbit(dims, frames, 10.0, W, H)
-    comp = [frame(c, "composite") for c in cams]
-    warm = frame(cams[-1], "composite")  # the last view again: everything cached
-    mip = []
-    for c in cams[:2]:
-        big = dict(c, width=W * 20, height=H * 20)
-        mip.append(frame(synth.wall_views(big, 20, 20)[210], "mip"))  # panel (10, 10) of 20 x 20
-    r.close()
-    tot = lambda xs, k: sum(x[k] for x in xs)  # noqa: E731
-    return {"workload": "4096x4096x8192 FP16 (256 GiB) streamed from the generator, 32 GiB cache, 1920x1080; "
-                        f"composite: {frames}-frame orbit (10 deg steps); MIP: central 1/400 panel of the "
-                        "view (bounded share of the cube), 2 orbit positions",
-            "h2d_link_gbs": h2d_gbs,
-            "composite_frames": comp, "composite_warm_repeat": warm, "mip_frames": mip,
-            "composite_orbit_s": tot(comp, "wall_s"), "composite_orbit_generate_s": tot(comp, "generate_s"),
-            "composite_orbit_floor_s": tot(comp, "floor_s"),
-            "mip_frame_s": [m["wall_s"] for m in mip], "mip_bricks": [m["bricks_fetched"] for m in mip],
-            "cold_frame_s": comp[0]["wall_s"], "warm_frame_s": warm["wall_s"],
-            "generate_gbs": tot(comp, "h2d_gb") / max(tot(comp, "generate_s"), 1e-9)}
+    return r, frame, dims, W, H, h2d_gbs
 
 
 # ------------------------------------------------------------------------------ our arm
@@ -920,6 +945,9 @@ def run_profile(a):
 
 def main():
     a = parse()
+    if a.ooc_full_mip:
+        run_ooc_full_mip(a)
+        return
     if a.profile:
         run_profile(a)
         return

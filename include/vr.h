@@ -338,7 +338,9 @@ vr_status vr_render_mip_noalloc(vr_ctx* ctx, float* out_rgba, float* out_max, vo
  * The callback fills dst (float32, x fastest) with the cube values of the
  * region [x0, x0+sx) x [y0, y0+sy) x [z0, z0+sz) and returns 0, or nonzero
  * on failure (the render then returns VR_ERR_IO).  It is called from the
- * thread that calls vr_render, one region at a time.
+ * thread that calls vr_render, one region at a time.  The library keeps fn and
+ * user (the one exception to keeping no caller pointer): both must stay valid
+ * until another cube is loaded or the context is destroyed.
  * Host waits (events, callbacks) are bounded by a deadline (default 120 s,
  * vr_set_stream_timeout); on expiry the call returns VR_ERR_TIMEOUT and the
  * context stays usable.  vr_render_backward and graph mode do not apply.

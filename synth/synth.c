@@ -12,8 +12,10 @@
  *
  *   noise  : i.i.d. Gaussian, sigma from the parameters, drawn by a
  *            counter-based generator (splitmix64 finaliser keyed by the seed
- *            and the global voxel index, Box-Muller with libm), so any region
- *            of the cube can be produced independently and bit-identically.
+ *            and the global voxel index; Box-Muller with libm, whose two
+ *            outputs serve the voxel pair 2m, 2m + 1 of the linear index), so
+ *            any region of the cube can be produced independently and
+ *            bit-identically.
  *   ripple : ripple_amp * sigma * sin(2 pi (z + 1/2) / ripple_period + phi),
  *            phi seeded; the same for every (x, y).  A smooth continuum
  *            residual along the channel axis.
@@ -23,6 +25,7 @@
  *            Amplitude, spatial FWHM, spectral FWHM and centre are uniform in
  *            the configured ranges.  Sources are added in index order.
  */
+#define _GNU_SOURCE /* sincos */
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
@@ -55,21 +58,35 @@ static inline uint64_t mix64(uint64_t z)
     return z ^ (z >> 31);
 }
 
-/* Uniform double in [0, 1) from (seed, stream, counter). */
+/* Key of stream `stream` of a seed; uniform double in [0, 1) from (key, counter). */
+static inline uint64_t stream_key(uint64_t seed, uint64_t stream)
+{
+    return mix64(seed ^ (stream * 0xD1B54A32D192ED03ull));
+}
+
+static inline double uni_k(uint64_t key, uint64_t ctr)
+{
+    return (double)(mix64(key + ctr) >> 11) * (1.0 / 9007199254740992.0);
+}
+
 static inline double uni(uint64_t seed, uint64_t stream, uint64_t ctr)
 {
-    uint64_t k = mix64(seed ^ (stream * 0xD1B54A32D192ED03ull));
-    uint64_t r = mix64(k + ctr);
-    return (double)(r >> 11) * (1.0 / 9007199254740992.0);
+    return uni_k(stream_key(seed, stream), ctr);
 }
 
 static const double TWO_PI = 6.283185307179586476925286766559;
 
-static inline double noise_at(uint64_t seed, uint64_t idx)
+/* Noise of voxels 2m and 2m + 1: both outputs of one Box-Muller transform of the
+ * uniforms at counters 4m and 4m + 1 of stream 0 (key). */
+static inline void noise_pair(uint64_t key, uint64_t m, double* n0, double* n1)
 {
-    double u1 = 1.0 - uni(seed, 0, 2 * idx);     /* (0, 1] */
-    double u2 = uni(seed, 0, 2 * idx + 1);
-    return sqrt(-2.0 * log(u1)) * cos(TWO_PI * u2);
+    const double u1 = 1.0 - uni_k(key, 4 * m); /* (0, 1] */
+    const double u2 = uni_k(key, 4 * m + 1);
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincos(TWO_PI * u2, &sn, &cs);
+    *n0 = r * cs;
+    *n1 = r * sn;
 }
 
 int syn_sources(const syn_params* p, syn_source* out)
@@ -123,6 +140,7 @@ static void* worker(void* arg)
 {
     job_t* j = (job_t*)arg;
     const syn_params* p = j->p;
+    const uint64_t key = stream_key(p->seed, 0);
     const int64_t sx = j->sx, sy = j->sy;
     double* acc = (double*)malloc(sizeof(double) * (size_t)(sx * sy));
     double* gx = (double*)malloc(sizeof(double) * (size_t)(sx > 0 ? sx : 1));
@@ -142,9 +160,22 @@ static void* worker(void* arg)
             const int64_t y = j->y0 + yr;
             const uint64_t row = ((uint64_t)z * (uint64_t)p->ny + (uint64_t)y) * (uint64_t)p->nx;
             double* a = acc + yr * sx;
-            for (int64_t xr = 0; xr < sx; ++xr) {
-                const uint64_t idx = row + (uint64_t)(j->x0 + xr);
-                a[xr] = p->sigma * noise_at(p->seed, idx) + rip;
+            const uint64_t i0 = row + (uint64_t)j->x0, i1 = i0 + (uint64_t)sx;
+            double n0, n1;
+            uint64_t i = i0;
+            if (i & 1) { /* the region starts on the second voxel of a pair */
+                noise_pair(key, i >> 1, &n0, &n1);
+                a[0] = p->sigma * n1 + rip;
+                ++i;
+            }
+            for (; i + 1 < i1; i += 2) {
+                noise_pair(key, i >> 1, &n0, &n1);
+                a[i - i0] = p->sigma * n0 + rip;
+                a[i + 1 - i0] = p->sigma * n1 + rip;
+            }
+            if (i < i1) {
+                noise_pair(key, i >> 1, &n0, &n1);
+                a[i - i0] = p->sigma * n0 + rip;
             }
         }
         for (int s = 0; s < p->nsrc; ++s) {
