@@ -666,7 +666,9 @@ k_brick_mip(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Br
 }
 
 // ---------------------------------------------------------------------------
-// Sort-last partial images through staged cells.
+// Sort-last partial images through staged cells: the images of the separately
+// rendered parts of a cube, combined afterwards (Abstract, Sec. 1), with the
+// bricks as the parts.
 //
 // The partial image of a brick holds, per pixel, the "over" composite from T = 1
 // of the ray's samples that the brick owns (the maximum of their values for
