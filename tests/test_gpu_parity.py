@@ -374,7 +374,7 @@ def test_brick_path_rejects_composite_and_small_bricks(vr):
     r.close()
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_survey_workload_sampled_pixels(vr, storage):
     """Full-size 1024 x 1024 x 2048 cube (2000 sources + ripple), perspective 1920 x 1080,
     two orbit frames; 4096 seeded pixels checked against the oracle, for the image-order
@@ -487,6 +487,20 @@ def test_sortlast_and_layered_composite(vr, storage):
     for i, c in enumerate(cams):
         compare(img[i].reshape(-1, 4), sc_off, c, "composite", tol=1e-4, path="sortlast")
     assert not img[3].any()
+    # the lane groups of other sizes join their runs in another rounding order
+    r = vr.Renderer(0, brick=brick)
+    r.set_path("sortlast")
+    r.load_cube(vol, storage)
+    r.set_transfer_function(tf, -1.0, 20.0)
+    r.set_camera(cams[1])
+    for group in (4, 16):
+        t = vr.vr_get_tuning(r.ctx)
+        t["group"] = group
+        vr.vr_set_tuning(r.ctx, t)
+        out = r.render("composite")
+        torch.cuda.synchronize()
+        compare(out[0].cpu().numpy().reshape(-1, 4), sc_off, cams[1], "composite", tol=1e-4, path="sortlast")
+    r.close()
     # a 1024-entry table: the partial images come from whole-brick marches instead of
     # staged cells (whose shared copy of the table holds at most 256 entries)
     dims, brick = (96, 80, 72), 32
