@@ -72,7 +72,10 @@ typedef enum { VR_COMPOSITE = 0, VR_MIP = 1 } vr_mode;
  *   partial images are folded per pixel front to back in visibility order
  *   (ascending sum |b - e| over axes, e the eye's brick; sign-weighted brick
  *   sum for orthographic views).  Early termination does not apply: the result
- *   is the composite with ert disabled.  VR_MIP: as VR_PATH_BRICK.
+ *   is the composite with ert disabled.  A brick's partial image is built from
+ *   its cells staged in shared memory, one pass per visibility key of the cells
+ *   within the brick (tables of more than 256 entries: whole-brick marches from
+ *   global memory, the same image up to rounding).  VR_MIP: as VR_PATH_BRICK.
  * VR_PATH_LAYERED: composite by bricks, one visibility layer per launch, each
  *   pixel's running (C, T) carried from layer to layer with per-sample early
  *   termination (the same image as VR_PATH_RAY); bricks of terminated pixels
