@@ -248,6 +248,15 @@ def test_degenerate_cubes(vr, dims):
         for i, c in enumerate(cams):
             compare(img[i].reshape(-1, 4), sc, c, mode, tol=1e-4,
                     gpu_max=mx[i] if mode == "mip" else None, max_tol=2e-3)
+    # staged cells (bricks of 32: one brick holding one ragged cell): brick-pass MIP and
+    # the sort-last partial passes
+    img, mx = _render(vr, vol, tf, cams, "mip", brick=32, path="brick")
+    for i, c in enumerate(cams):
+        compare(img[i].reshape(-1, 4), sc, c, "mip", tol=1e-4, gpu_max=mx[i], max_tol=2e-3, path="brick")
+    sc_off = oracle.Scene(vol, tf, -1.0, 20.0, 0.5, 2.0)
+    img, _ = _render(vr, vol, tf, cams, "composite", brick=32, path="sortlast")
+    for i, c in enumerate(cams):
+        compare(img[i].reshape(-1, 4), sc_off, c, "composite", tol=1e-4, path="sortlast")
 
 
 def test_many_cameras_and_sample_count(vr):
