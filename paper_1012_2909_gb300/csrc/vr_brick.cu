@@ -803,6 +803,10 @@ __device__ __forceinline__ void march_part(const BrickParams& P, const T* tile, 
         } else {
             const int L = (n + G - 1) / G;  // samples per lane: lane r takes [r L, r L + L)
             const int iters = (int)__reduce_max_sync(0xffffffffu, (unsigned int)L);
+            // the slot's state, read before the march (no other record of this pass
+            // writes it), so that its latency hides behind the samples
+            float4 p = make_float4(0.f, 0.f, 0.f, 1.f);
+            if (writer) p = __ldcg(P.partial + s.pix);
             float C0, C1, C2, Tr;
             if (clamp)
                 run_over<T, true>(tile, s_tf, tf, s, n, r * L, L, iters, C0, C1, C2, Tr);
@@ -823,7 +827,6 @@ __device__ __forceinline__ void march_part(const BrickParams& P, const T* tile, 
                 }
             }
             if (writer) {
-                float4 p = P.partial[s.pix];
                 p.x = fmaf(p.w, C0, p.x);
                 p.y = fmaf(p.w, C1, p.y);
                 p.z = fmaf(p.w, C2, p.z);
